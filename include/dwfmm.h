@@ -1,0 +1,205 @@
+/*
+ * dwfmm.h -- C ABI of the GB300 dimension-weighted fast multipole method.
+ *
+ * Harbrecht, Multerer, Quizi, "The dimension weighted fast multipole method
+ * for scattered data approximation" (arXiv 2402.09531).
+ *
+ * The library computes y = K_tilde x, the DW-FMM approximation of the dense
+ * kernel matrix K = [phi(||x_i - x_j|| / sigma)] applied to R right-hand
+ * sides (Sec. 5.2, Eq. (5.4)), and solves (K_tilde + lambda I) c = f by
+ * conjugate gradients (Sec. 2, Eq. (2.2); Sec. 6.2).  Every numerical step
+ * runs in CUDA kernels on one GPU; the host only validates arguments, sizes
+ * allocations and sequences launches.
+ *
+ * Conventions shared by every entry point:
+ *  - No exception crosses the ABI: every call returns a dwfmm_status.  A
+ *    failed call leaves the plan in a state that dwfmm_plan_destroy accepts.
+ *  - The caller owns every buffer it passes in, and the stream.  Pointers
+ *    marked "host or device" may point to either; the library detects the
+ *    kind with cudaPointerGetAttributes and stages host data through its own
+ *    device buffers (copies are enqueued on the given stream).
+ *  - The plan owns the tree-ordered copy of the sites, the interaction
+ *    lists, the expansion data (nodes, V^{-1}) and all workspace.  It keeps
+ *    no pointer given by the caller after a call returns.
+ *  - A plan is used by one host thread and one stream at a time.
+ *  - `stream` is a cudaStream_t passed as void*; NULL means the legacy
+ *    default stream.  Calls return once the work is enqueued, except where
+ *    stated (tree_build and solve synchronise the stream).
+ *  - Matrices of right-hand sides are column-major N x R with a leading
+ *    dimension ld >= N: entry (i, r) lives at x[r * ld + i], in the caller's
+ *    site order.  Sites are row-major N x d with leading dimension ld >= d:
+ *    coordinate k of site i lives at pts[i * ld + k].
+ */
+#ifndef DWFMM_H
+#define DWFMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DWFMM_OK = 0,
+  DWFMM_ERR_INVALID_ARG = 1,   /* a NULL pointer, a size out of range, NaN/Inf sites */
+  DWFMM_ERR_OOM = 2,           /* a device allocation failed */
+  DWFMM_ERR_CUDA = 3,          /* a CUDA runtime call failed */
+  DWFMM_ERR_BREAKDOWN = 4,     /* CG: p^T (K_tilde + lambda I) p <= 0 */
+  DWFMM_ERR_NOT_CONVERGED = 5, /* CG: maxit reached before rtol */
+  DWFMM_ERR_TIMEOUT = 6,       /* a bounded device wait gave up */
+  DWFMM_ERR_STATE = 7,         /* call out of order (e.g. matvec before tree_build) */
+  DWFMM_ERR_SINGULAR = 8       /* the Halton candidates were not unisolvent */
+} dwfmm_status;
+
+/* Radial kernels phi(r), evaluated at r = ||x - y||_2 / sigma.
+ * Sec. 6.2 prints exp(+r); the positive definite exp(-r) is used (Def. 2.2). */
+typedef enum {
+  DWFMM_K_EXP = 0,       /* exp(-r) */
+  DWFMM_K_MATERN32 = 1,  /* (1 + sqrt(3) r) exp(-sqrt(3) r) */
+  DWFMM_K_GAUSS = 2      /* exp(-r^2 / 2) */
+} dwfmm_kernel;
+
+/* Arithmetic of the matvec.  FP64: every phase in float64.  FP32: near field
+ * (P2P), couplings (M2L) and expansions in float32 with compensated
+ * accumulation.  MIXED: FP32 plus the V^{-1} moment/local conversions on
+ * tensor cores in BF16 with FP32 accumulation.  CG dot products and
+ * vectors are float64 in every mode. */
+typedef enum {
+  DWFMM_P_FP64 = 0,
+  DWFMM_P_FP32 = 1,
+  DWFMM_P_MIXED = 2
+} dwfmm_precision;
+
+/* Rule for the weights omega_k of the index set Lambda (Sec. 4).
+ *  INV_GAMMA:    omega_k = gamma_1 / gamma_k.
+ *  PAPER_LOGRHO: Sec. 6.2, tau_k = 1 / (eta b_k) with b_k = 2 gamma_k,
+ *                rho_k = e rho(tau_k) / rho(tau_1), omega_k = log rho_k,
+ *                rho(tau) = 2 tau + sqrt(1 + 4 tau^2) (Lemma 4.1).
+ *  EXPLICIT:     omega_k = weights[k]. */
+typedef enum {
+  DWFMM_W_INV_GAMMA = 0,
+  DWFMM_W_PAPER_LOGRHO = 1,
+  DWFMM_W_EXPLICIT = 2
+} dwfmm_weight_rule;
+
+/* Plan parameters.  All fields are read during dwfmm_plan_create only. */
+typedef struct {
+  int32_t d;                  /* dimension, 1..32 */
+  int32_t kernel;             /* dwfmm_kernel */
+  double sigma;               /* length scale, > 0 */
+  const double* gamma;        /* host, d dimension weights gamma_k > 0 (Sec. 2, Eq. (2.3)) */
+  int32_t weight_rule;        /* dwfmm_weight_rule */
+  const double* weights;      /* host, d weights if EXPLICIT, else ignored */
+  double q;                   /* degree of Lambda_{omega,q,d}, >= 0 (Sec. 4) */
+  double eta;                 /* admissibility parameter, > 0 (Eq. (5.1)) */
+  int32_t leaf_size;          /* max sites per leaf, 2..1024 (Sec. 5.1) */
+  int32_t halton_candidates;  /* Halton candidates M; <= 0 selects max(2000, 10 n) (Sec. 5.4) */
+  int32_t precision;          /* dwfmm_precision */
+  int32_t max_rhs;            /* largest R passed to matvec/solve, 1..64 */
+} dwfmm_config;
+
+typedef struct dwfmm_plan_s* dwfmm_plan;
+
+/* Create a plan: weights, the index set Lambda_{omega,q,d} (Sec. 4, enumerated
+ * lexicographically in (alpha_1..alpha_d)), Halton candidates, approximate
+ * Fekete nodes by greedy column-pivoted QR of the Vandermonde matrix on the
+ * candidates (Sec. 5.4), V (Eq. (5.3)) and V^{-1} by Gauss-Jordan with
+ * partial pivoting.  The candidate, QR and inversion steps run on the GPU in
+ * float64.  Synchronises `stream`.  On success *out receives the plan.
+ * Errors: INVALID_ARG (bad config), SINGULAR, OOM, CUDA. */
+dwfmm_status dwfmm_plan_create(const dwfmm_config* cfg, void* stream, dwfmm_plan* out);
+
+/* Replace the interpolation nodes by `nodes` (host, n x d row-major, in
+ * [0,1]^d) and recompute V^{-1} on the GPU.  n must equal the index-set size.
+ * Used to separate matvec parity from node-selection parity.  Must be called
+ * before dwfmm_tree_build.  Synchronises `stream`. */
+dwfmm_status dwfmm_plan_set_nodes(dwfmm_plan plan, const double* nodes, int64_t n, void* stream);
+
+/* Build the cluster tree (Sec. 5.1: split along the longest bounding-box edge
+ * into halves of ceil/floor size, the first half holding the sites smallest
+ * by (x_k, position), stable), the far/near lists (Eq. (5.1): nu x nu' is far
+ * iff admissible and its parent pair is not; near = non-admissible leaf
+ * pairs; a pair at distance 0 is never admissible) and the per-cluster
+ * expansion data.  `pts` (host or device) holds N x d sites, row-major with
+ * leading dimension ld >= d; it is copied.  N = 0 is valid (matvec then does
+ * nothing).  Replaces any previous tree.  Synchronises `stream`.
+ * Errors: INVALID_ARG (NULL, ld < d, N < 0, non-finite site), OOM, CUDA. */
+dwfmm_status dwfmm_tree_build(dwfmm_plan plan, const double* pts, int64_t n, int64_t ld,
+                              void* stream);
+
+/* y = K_tilde x for R = nrhs right-hand sides (Eq. (5.4), nested bases):
+ * P2M, M2M, M2L, L2L, L2P on the far field plus the dense P2P near field.
+ * x, y (host or device): float64, column-major N x R, leading dims ldx, ldy
+ * >= N, caller's site order.  x and y must not overlap.  With device
+ * pointers the call returns once the work is enqueued on `stream`; with a
+ * host y it synchronises `stream` before returning.
+ * Errors: STATE (no tree), INVALID_ARG (nrhs outside 1..max_rhs, ld < N,
+ * NULL), CUDA. */
+dwfmm_status dwfmm_matvec(dwfmm_plan plan, const double* x, double* y, int32_t nrhs,
+                          int64_t ldx, int64_t ldy, void* stream);
+
+/* Solve (K_tilde + lambda I) c = f for R = nrhs right-hand sides by
+ * unpreconditioned conjugate gradients from c = 0 (Sec. 2 Eq. (2.2),
+ * Sec. 6.2), float64 vectors and dot products, one CG per column.
+ * Each column stops when its recurrence residual satisfies
+ * ||r|| <= rtol ||f||.  For FP32/MIXED plans the solve runs iterative
+ * refinement: the residual f - (K_tilde + lambda I) c is recomputed with the
+ * float64 operator and an inner CG in the plan's precision corrects c, until
+ * the float64 relative residual is <= rtol.  f, c (host or device):
+ * float64, column-major N x R with leading dimension ld >= N.
+ * iters_out (host, may be NULL): total CG iterations; relres_out (host, R
+ * values, may be NULL): final true relative residual per column.
+ * Synchronises `stream`.
+ * Errors: STATE, INVALID_ARG (lambda < 0, rtol <= 0, maxit < 1), BREAKDOWN,
+ * NOT_CONVERGED, CUDA. */
+dwfmm_status dwfmm_solve(dwfmm_plan plan, double lambda, const double* f, double* c,
+                         int32_t nrhs, int64_t ld, double rtol, int32_t maxit,
+                         int32_t* iters_out, double* relres_out, void* stream);
+
+/* Release every resource of the plan (NULL is accepted).  Synchronises the
+ * plan's last stream first. */
+dwfmm_status dwfmm_plan_destroy(dwfmm_plan plan);
+
+/* Static description of a status code. */
+const char* dwfmm_status_string(dwfmm_status s);
+
+/* Message of the last failed call on this plan ("" if none). */
+const char* dwfmm_last_error(dwfmm_plan plan);
+
+/* Sizes: n_x = |Lambda|, n_far / n_near = block counts, depth = J.
+ * Any output pointer may be NULL.  depth = -1 before tree_build. */
+dwfmm_status dwfmm_plan_info(dwfmm_plan plan, int64_t* n_x, int64_t* n_far, int64_t* n_near,
+                             int32_t* depth);
+
+/* Copy out plan data (host buffers, NULL to skip), for tests and tools:
+ *  weights: d doubles; lam: n x d int32 multi-indices (row-major);
+ *  nodes: n x d doubles; pivots: n int32 Halton indices (0-based, -1 if the
+ *  nodes were set by dwfmm_plan_set_nodes); vinv: n x n doubles, row-major. */
+dwfmm_status dwfmm_plan_export(dwfmm_plan plan, double* weights, int32_t* lam, double* nodes,
+                               int32_t* pivots, double* vinv);
+
+/* Copy out the tree (host buffers, NULL to skip): perm (N int64, tree
+ * position -> caller index), begin/end (2^{J+1}-1 int64 each, heap order:
+ * level j holds clusters 2^j-1 .. 2^{j+1}-2), lo/hi (clusters x d doubles). */
+dwfmm_status dwfmm_tree_export(dwfmm_plan plan, int64_t* perm, int64_t* begin, int64_t* end,
+                               double* lo, double* hi);
+
+/* Copy out the lists (host buffers, NULL to skip): far (n_far x 2 int32
+ * (target, source) cluster ids sorted by level, target, source) and near
+ * (n_near x 2 int32, sorted by target, source). */
+dwfmm_status dwfmm_lists_export(dwfmm_plan plan, int32_t* far, int32_t* near);
+
+/* Phase timing.  With enable != 0 every later matvec records CUDA events on
+ * the streams that launch each phase; dwfmm_phase_times returns, per phase,
+ * the summed milliseconds since the last reset and the launch counts:
+ * ms[0] gather, [1] P2M+M2M, [2] M2L, [3] L2L+L2P, [4] P2P, [5] scatter,
+ * [6] whole matvec; launches[i] the number of kernel launches of phase i.
+ * Reading the times synchronises the plan's streams. */
+dwfmm_status dwfmm_set_profiling(dwfmm_plan plan, int32_t enable);
+dwfmm_status dwfmm_phase_times(dwfmm_plan plan, double* ms, int64_t* launches, int32_t reset);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DWFMM_H */

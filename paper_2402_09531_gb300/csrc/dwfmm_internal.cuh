@@ -1,0 +1,223 @@
+// Internal declarations of the GB300 DW-FMM library (not part of the ABI).
+//
+// Data layout in HBM (all arrays owned by the plan):
+//   clusters   heap order: level j holds clusters 2^j-1 .. 2^{j+1}-2,
+//              children of c are 2c+1, 2c+2; the leaves are level J.
+//   sites      leaf-blocked SoA: pts[leaf][k][m_pad], m_pad a multiple of 8
+//              (every leaf block starts on a 32-byte boundary, so one
+//              leaf is one contiguous bulk copy); slots past the leaf's
+//              count hold copies of its first site and zero charges.
+//   charges    xb[leaf][r][m_pad]      (right-hand sides, tree order)
+//   nodes      ynode[c][k][n_pad]      (a_c(xi_alpha), Sec. 5.2)
+//   moments    mom[c][r][n_pad]        (V^{-T} P_c^T x: charges at the nodes)
+//   locals     loc[c][r][n_pad]        (sum_s S_{c,s} mom_s: potentials at the nodes)
+//              lco[c][r][n_pad]        (V^{-1} loc + inherited: Legendre coefficients)
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/dwfmm.h"
+
+namespace dw {
+
+constexpr int kMaxDim = 32;
+constexpr int kRC = 16;  // right-hand sides per kernel pass
+
+struct CudaError {
+  cudaError_t err;
+  const char* what;
+};
+
+#define DW_CUDA(call)                                                          \
+  do {                                                                         \
+    cudaError_t _e = (call);                                                   \
+    if (_e != cudaSuccess) throw ::dw::CudaError{_e, #call};                   \
+  } while (0)
+
+struct ApiError {
+  dwfmm_status status;
+  std::string msg;
+};
+
+inline void fail(dwfmm_status s, const std::string& m) { throw ApiError{s, m}; }
+
+// Device buffer with explicit lifetime (freed by the plan).
+template <class T>
+struct DBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  DBuf() = default;
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  DBuf(DBuf&& o) noexcept : p(o.p), n(o.n) {
+    o.p = nullptr;
+    o.n = 0;
+  }
+  DBuf& operator=(DBuf&& o) noexcept {
+    if (this != &o) {
+      release();
+      p = o.p;
+      n = o.n;
+      o.p = nullptr;
+      o.n = 0;
+    }
+    return *this;
+  }
+  ~DBuf() { release(); }
+  void alloc(size_t count) {
+    if (count <= n && p) return;
+    release();
+    if (count == 0) return;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&p), count * sizeof(T));
+    if (e != cudaSuccess) {
+      p = nullptr;
+      n = 0;
+      (void)cudaGetLastError();
+      fail(DWFMM_ERR_OOM, "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes failed");
+    }
+    n = count;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+};
+
+// Expansion tables shared by all clusters (device pointers).
+struct ExpDev {
+  int n;            // |Lambda|
+  int n_pad;        // n rounded up to a multiple of 8
+  int d;
+  int lsum;         // sum_k (q_k + 1): Legendre values per point
+  int nnz_max;      // max nonzeros of a multi-index
+  const int16_t* fac;   // [n][nnz_max] offsets into a point's Legendre table, -1 = none
+  const int32_t* qk;    // [d] max degree per dimension
+  const int32_t* loff;  // [d] offset of dimension k in a point's Legendre table
+};
+
+struct TreeDev {
+  int64_t N;
+  int J;
+  int L;        // 2^J leaves
+  int C;        // 2^{J+1} - 1 clusters
+  int m_pad;
+  const int32_t* begin;   // [C] first tree position
+  const int32_t* count;   // [C] sites
+};
+
+struct TimerRec {
+  int phase;
+  cudaEvent_t a, b;
+  int launches;
+};
+
+struct Timers {
+  bool on = false;
+  std::vector<cudaEvent_t> open;
+  std::vector<TimerRec> recs;
+  double ms[8] = {0};
+  int64_t launches[8] = {0};
+};
+
+struct Plan {
+  // configuration
+  int d = 0, kernel = 0, wrule = 0, leaf = 0, M = 0, prec = 0, max_rhs = 0;
+  double sigma = 1.0, q = 0.0, eta = 1.0;
+  std::vector<double> gamma, w;
+  cudaStream_t stream = nullptr;   // stream of the last call
+  cudaStream_t side = nullptr;     // near field runs here, concurrently with the far field
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  int device = 0;
+  std::string last_error;
+
+  // expansion (Sec. 4, 5.2, 5.4)
+  int n = 0, n_pad = 0, lsum = 0, nnz_max = 0;
+  std::vector<int32_t> lam;       // [n][d]
+  std::vector<int32_t> qk, loff;
+  std::vector<int32_t> pivots;    // [n], -1 if set by the caller
+  DBuf<int16_t> d_fac;
+  DBuf<int32_t> d_qk, d_loff, d_lam;
+  DBuf<double> d_nodes;           // [n][d]
+  DBuf<double> d_vinv;            // [n_pad][n_pad] row-major, zero padded
+  DBuf<float> d_vinv32;
+  bool have_nodes = false;
+
+  // tree (Sec. 5.1)
+  bool have_tree = false;
+  int64_t N = 0;
+  int J = -1, L = 0, C = 0, m_pad = 0, jmin = 0;
+  std::vector<int32_t> h_begin, h_count;
+  DBuf<int32_t> d_begin, d_count;
+  DBuf<int32_t> d_perm;           // tree position -> caller index
+  DBuf<double> d_lo, d_hi, d_ext;  // [C][d]
+  DBuf<float> d_lo32, d_iext32;    // [C][d]
+  DBuf<double> d_iext;             // [C][d]
+  DBuf<double> d_pts64;           // [L][d][m_pad]
+  DBuf<float> d_pts32;
+  DBuf<double> d_ynode64;         // [C][d][n_pad]
+  DBuf<float> d_ynode32;
+  // lists (Eq. (5.1)), CSR by target
+  int64_t nfar = 0, nnear = 0;
+  std::vector<int64_t> far_level_count;
+  DBuf<int32_t> d_far_rowptr, d_far_col;    // [C+1], [nfar]  (sources: cluster ids)
+  DBuf<int32_t> d_near_rowptr, d_near_col;  // [L+1], [nnear] (sources: leaf index)
+  DBuf<int32_t> d_far_pairs, d_near_pairs;  // for export: [nfar][2], [nnear][2]
+
+  // matvec workspace, float64 and float32 variants
+  DBuf<double> xb64, ynear64, yfar64, mom64, loc64, lco64;
+  DBuf<float> xb32, ynear32, yfar32, mom32, loc32, lco32;
+  DBuf<double> stage_in, stage_out;   // host-pointer staging
+  // solve workspace
+  DBuf<double> cg_r, cg_p, cg_ap, cg_c, cg_f, cg_dot, cg_tmp;
+
+  // scratch for tree build
+  DBuf<unsigned char> scratch;
+
+  Timers tm;
+
+  ExpDev exp_dev() const {
+    return ExpDev{n, n_pad, d, lsum, nnz_max, d_fac.p, d_qk.p, d_loff.p};
+  }
+  TreeDev tree_dev() const { return TreeDev{N, J, L, C, m_pad, d_begin.p, d_count.p}; }
+  void free_tree();
+  void free_all();
+};
+
+// ---- setup (setup.cu) ----
+void setup_expansion(Plan& P);              // weights, Lambda, tables (host) + nodes/V^{-1} (GPU)
+void setup_vinv_from_nodes(Plan& P);         // V and V^{-1} on the GPU from d_nodes
+
+// ---- tree and lists (tree.cu) ----
+void build_tree(Plan& P, const double* pts_dev, int64_t n, int64_t ld);
+void build_lists(Plan& P);
+void build_cluster_data(Plan& P);           // extents, nodes, leaf-blocked sites
+
+// ---- matvec (farfield.cu, nearfield.cu, matvec.cu) ----
+// x, y: device, caller order, column-major.
+void matvec_device(Plan& P, const double* x, int64_t ldx, double* y, int64_t ldy, int R, bool fp64);
+void ensure_workspace(Plan& P, bool fp64);
+void farfield_set_smem_limits(Plan& P);
+size_t farfield_smem_need(const Plan& P, bool fp64);
+void launch_gather(Plan& P, const double* x, int64_t ldx, int r0, int Rc, bool fp64);
+void launch_scatter(Plan& P, double* y, int64_t ldy, int r0, int Rc, bool fp64);
+void launch_farfield(Plan& P, int Rc, bool fp64);
+void launch_m2l(Plan& P, int Rc, bool fp64);
+void launch_nearfield(Plan& P, int Rc, bool fp64, cudaStream_t s);
+
+// ---- solve (solve.cu) ----
+dwfmm_status solve(Plan& P, double lambda, const double* f, double* c, int R, int64_t ld,
+                   double rtol, int maxit, int* iters, double* relres);
+
+inline int ceil_div(int64_t a, int64_t b) { return static_cast<int>((a + b - 1) / b); }
+inline int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+// timers (matvec.cu): CUDA events on the launching stream, per phase
+void timer_begin(Plan& P, int phase, cudaStream_t s);
+void timer_end(Plan& P, int phase, cudaStream_t s, int launches);
+void timers_collect(Plan& P);
+
+}  // namespace dw

@@ -1,0 +1,233 @@
+// Conjugate gradients for (K_tilde + lambda I) c = f (Sec. 2 Eq. (2.2);
+// Sec. 6.2 solves the kernel ridge system by CG to a relative tolerance).
+// One independent CG per right-hand side column, float64 vectors, dot
+// products reduced deterministically (fixed block partition, fixed order).
+// FP32/MIXED plans run iterative refinement: the outer residual uses the
+// float64 operator, the inner CG the plan's reduced-precision operator.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "dwfmm_internal.cuh"
+
+namespace dw {
+
+namespace {
+
+constexpr int kDotThreads = 256;
+constexpr int kDotBlocks = 120;
+
+__global__ void k_dot_partial(const double* a, const double* b, int64_t n, int64_t ld, double* part) {
+  __shared__ double sh[kDotThreads / 32];
+  const int r = blockIdx.y;
+  const double* x = a + r * ld;
+  const double* y = b + r * ld;
+  double s = 0.0;
+  for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    s += x[i] * y[i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kDotThreads / 32; ++w) t += sh[w];
+    part[r * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+__global__ void k_dot_final(const double* part, int nb, int R, double* out) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= R) return;
+  double t = 0.0;
+  for (int b = 0; b < nb; ++b) t += part[r * nb + b];
+  out[r] = t;
+}
+
+// y[:, r] = a * x[:, r] + b * y[:, r] (+ lam * z[:, r] if z)
+__global__ void k_axpby(const double* x, double* y, const double* z, const double* coef_a,
+                        double coef_b_const, const double* coef_b, double lam, int64_t n, int64_t ld,
+                        int R, double a_sign) {
+  const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= n * R) return;
+  const int r = static_cast<int>(t / n);
+  const int64_t i = t % n;
+  const int64_t o = r * ld + i;
+  const double a = coef_a ? a_sign * coef_a[r] : a_sign;
+  const double bb = coef_b ? coef_b[r] : coef_b_const;
+  double v = a * x[o] + bb * y[o];
+  if (z) v += lam * z[o];
+  y[o] = v;
+}
+
+struct Vecs {
+  double *c, *r, *p, *ap, *part, *dot, *coef;
+};
+
+void dots(Plan& P, const double* a, const double* b, int64_t n, int64_t ld, int R, double* part,
+          double* out_dev, double* out_host) {
+  dim3 grid(kDotBlocks, R);
+  k_dot_partial<<<grid, kDotThreads, 0, P.stream>>>(a, b, n, ld, part);
+  k_dot_final<<<ceil_div(R, 64), 64, 0, P.stream>>>(part, kDotBlocks, R, out_dev);
+  DW_CUDA(cudaMemcpyAsync(out_host, out_dev, R * sizeof(double), cudaMemcpyDeviceToHost, P.stream));
+  DW_CUDA(cudaStreamSynchronize(P.stream));
+}
+
+// A v = K_tilde v + lam v (into out); v, out: n x R, leading dimension n.
+void apply_op(Plan& P, const double* v, double* out, int R, double lam, bool fp64) {
+  const int64_t n = P.N;
+  matvec_device(P, v, n, out, n, R, fp64);
+  if (lam != 0.0)
+    // out = lam * v + 1 * out  (a_sign carries lam, coef_b_const = 1)
+    k_axpby<<<ceil_div(n * R, 256), 256, 0, P.stream>>>(v, out, nullptr, nullptr, 1.0, nullptr, 0.0, n, n, R, lam);
+}
+
+// Plain CG on (K_tilde + lam I) x = b with x0 = 0, columns independent.
+// Returns iterations; per-column status in st (0 ok, 1 breakdown, 2 not converged).
+int cg(Plan& P, Vecs& V, const double* b, double* x, int R, double lam, double rtol, int maxit,
+       bool fp64, std::vector<int>& st) {
+  const int64_t n = P.N;
+  const int64_t nr = n * R;
+  std::vector<double> rr(R), rr_new(R), pap(R), bn(R), alpha(R), beta(R);
+  DW_CUDA(cudaMemsetAsync(x, 0, nr * sizeof(double), P.stream));
+  DW_CUDA(cudaMemcpyAsync(V.r, b, nr * sizeof(double), cudaMemcpyDeviceToDevice, P.stream));
+  DW_CUDA(cudaMemcpyAsync(V.p, b, nr * sizeof(double), cudaMemcpyDeviceToDevice, P.stream));
+  dots(P, V.r, V.r, n, n, R, V.part, V.dot, rr.data());
+  st.assign(R, 2);
+  std::vector<char> active(R, 1);
+  for (int r = 0; r < R; ++r) {
+    bn[r] = std::sqrt(rr[r]);
+    if (bn[r] == 0.0 || std::sqrt(rr[r]) <= rtol * bn[r]) {
+      active[r] = 0;
+      st[r] = 0;
+    }
+  }
+  int it = 0;
+  for (; it < maxit; ++it) {
+    bool any = false;
+    for (int r = 0; r < R; ++r) any |= active[r] != 0;
+    if (!any) break;
+    apply_op(P, V.p, V.ap, R, lam, fp64);
+    dots(P, V.p, V.ap, n, n, R, V.part, V.dot, pap.data());
+    for (int r = 0; r < R; ++r) {
+      alpha[r] = 0.0;
+      if (!active[r]) continue;
+      if (!(pap[r] > 0.0)) {
+        active[r] = 0;
+        st[r] = 1;
+        continue;
+      }
+      alpha[r] = rr[r] / pap[r];
+    }
+    DW_CUDA(cudaMemcpyAsync(V.coef, alpha.data(), R * sizeof(double), cudaMemcpyHostToDevice, P.stream));
+    // x += alpha p ; r -= alpha Ap
+    k_axpby<<<ceil_div(nr, 256), 256, 0, P.stream>>>(V.p, x, nullptr, V.coef, 1.0, nullptr, 0.0, n, n, R, 1.0);
+    k_axpby<<<ceil_div(nr, 256), 256, 0, P.stream>>>(V.ap, V.r, nullptr, V.coef, 1.0, nullptr, 0.0, n, n, R, -1.0);
+    dots(P, V.r, V.r, n, n, R, V.part, V.dot, rr_new.data());
+    for (int r = 0; r < R; ++r) {
+      beta[r] = 0.0;
+      if (!active[r]) continue;
+      if (std::sqrt(rr_new[r]) <= rtol * bn[r]) {
+        active[r] = 0;
+        st[r] = 0;
+      }
+      beta[r] = rr_new[r] / rr[r];
+      rr[r] = rr_new[r];
+    }
+    DW_CUDA(cudaMemcpyAsync(V.coef, beta.data(), R * sizeof(double), cudaMemcpyHostToDevice, P.stream));
+    // p = r + beta p
+    k_axpby<<<ceil_div(nr, 256), 256, 0, P.stream>>>(V.r, V.p, nullptr, nullptr, 0.0, V.coef, 0.0, n, n, R, 1.0);
+  }
+  DW_CUDA(cudaGetLastError());
+  return it;
+}
+
+}  // namespace
+
+dwfmm_status solve(Plan& P, double lam, const double* f, double* c, int R, int64_t ld, double rtol,
+                   int maxit, int* iters, double* relres) {
+  const int64_t n = P.N;
+  const int64_t nr = n * R;
+  if (n == 0) {
+    if (iters) *iters = 0;
+    if (relres)
+      for (int r = 0; r < R; ++r) relres[r] = 0.0;
+    return DWFMM_OK;
+  }
+  P.cg_r.alloc(nr);
+  P.cg_p.alloc(nr);
+  P.cg_ap.alloc(nr);
+  P.cg_c.alloc(nr);
+  P.cg_f.alloc(nr);
+  P.cg_tmp.alloc(nr);
+  P.cg_dot.alloc(static_cast<size_t>(kDotBlocks) * R + 2 * R + 2);
+  Vecs V{P.cg_c.p, P.cg_r.p, P.cg_p.p, P.cg_ap.p, P.cg_dot.p, P.cg_dot.p + kDotBlocks * R,
+         P.cg_dot.p + kDotBlocks * R + R};
+  // compact copy of f (leading dimension n)
+  DW_CUDA(cudaMemcpy2DAsync(P.cg_f.p, n * sizeof(double), f, ld * sizeof(double), n * sizeof(double), R,
+                            cudaMemcpyDeviceToDevice, P.stream));
+  std::vector<double> fn2(R), res2(R);
+  dots(P, P.cg_f.p, P.cg_f.p, n, n, R, V.part, V.dot, fn2.data());
+  const bool fp64 = P.prec == DWFMM_P_FP64;
+  int total_it = 0;
+  std::vector<int> st;
+  dwfmm_status status = DWFMM_OK;
+  if (fp64) {
+    total_it = cg(P, V, P.cg_f.p, V.c, R, lam, rtol, maxit, true, st);
+    for (int r = 0; r < R; ++r) {
+      if (st[r] == 1) status = DWFMM_ERR_BREAKDOWN;
+      else if (st[r] == 2 && status == DWFMM_OK) status = DWFMM_ERR_NOT_CONVERGED;
+    }
+  } else {
+    // iterative refinement: c += CG32(f - A64 c)
+    DW_CUDA(cudaMemsetAsync(V.c, 0, nr * sizeof(double), P.stream));
+    DBuf<double> delta, rhs;
+    delta.alloc(nr);
+    rhs.alloc(nr);
+    DW_CUDA(cudaMemcpyAsync(rhs.p, P.cg_f.p, nr * sizeof(double), cudaMemcpyDeviceToDevice, P.stream));
+    const double inner_tol = std::max(rtol, 1e-5);
+    status = DWFMM_ERR_NOT_CONVERGED;
+    for (int outer = 0; outer < 50 && total_it < maxit; ++outer) {
+      dots(P, rhs.p, rhs.p, n, n, R, V.part, V.dot, res2.data());
+      bool done = true;
+      for (int r = 0; r < R; ++r) done &= std::sqrt(res2[r]) <= rtol * std::sqrt(fn2[r]) || fn2[r] == 0.0;
+      if (done) {
+        status = DWFMM_OK;
+        break;
+      }
+      const int it = cg(P, V, rhs.p, delta.p, R, lam, inner_tol, maxit - total_it, false, st);
+      total_it += it;
+      bool broke = false;
+      for (int r = 0; r < R; ++r) broke |= st[r] == 1;
+      k_axpby<<<ceil_div(nr, 256), 256, 0, P.stream>>>(delta.p, V.c, nullptr, nullptr, 1.0, nullptr, 0.0, n, n, R, 1.0);
+      // rhs = f - (K64 c + lam c)
+      apply_op(P, V.c, P.cg_tmp.p, R, lam, true);
+      DW_CUDA(cudaMemcpyAsync(rhs.p, P.cg_f.p, nr * sizeof(double), cudaMemcpyDeviceToDevice, P.stream));
+      k_axpby<<<ceil_div(nr, 256), 256, 0, P.stream>>>(P.cg_tmp.p, rhs.p, nullptr, nullptr, 1.0, nullptr, 0.0, n, n, R, -1.0);
+      if (broke) {
+        status = DWFMM_ERR_BREAKDOWN;
+        break;
+      }
+    }
+    if (status == DWFMM_ERR_NOT_CONVERGED) {
+      dots(P, rhs.p, rhs.p, n, n, R, V.part, V.dot, res2.data());
+      bool done = true;
+      for (int r = 0; r < R; ++r) done &= std::sqrt(res2[r]) <= rtol * std::sqrt(fn2[r]) || fn2[r] == 0.0;
+      if (done) status = DWFMM_OK;
+    }
+  }
+  // true residual with the float64 operator
+  apply_op(P, V.c, P.cg_tmp.p, R, lam, true);
+  DW_CUDA(cudaMemcpyAsync(P.cg_r.p, P.cg_f.p, nr * sizeof(double), cudaMemcpyDeviceToDevice, P.stream));
+  k_axpby<<<ceil_div(nr, 256), 256, 0, P.stream>>>(P.cg_tmp.p, P.cg_r.p, nullptr, nullptr, 1.0, nullptr, 0.0, n, n, R, -1.0);
+  dots(P, P.cg_r.p, P.cg_r.p, n, n, R, V.part, V.dot, res2.data());
+  if (relres)
+    for (int r = 0; r < R; ++r) relres[r] = fn2[r] > 0.0 ? std::sqrt(res2[r] / fn2[r]) : 0.0;
+  if (iters) *iters = total_it;
+  DW_CUDA(cudaMemcpy2DAsync(c, ld * sizeof(double), V.c, n * sizeof(double), n * sizeof(double), R,
+                            cudaMemcpyDeviceToDevice, P.stream));
+  DW_CUDA(cudaStreamSynchronize(P.stream));
+  return status;
+}
+
+}  // namespace dw

@@ -1,0 +1,229 @@
+"""ctypes binding of the C ABI in include/dwfmm.h (argument marshalling only).
+
+Every function keeps the C name and returns the C status; ``check`` turns a
+non-zero status into :class:`DwfmmError`.  The :class:`Plan` helper wraps the
+calls for torch tensors (device or host) and numpy arrays.  All numerical
+work runs in libdwfmm.so; importing this module without the built library
+raises immediately (there is no fallback path).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdwfmm.so")
+
+OK = 0
+ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_BREAKDOWN, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR_STATE, \
+    ERR_SINGULAR = range(1, 9)
+K_EXP, K_MATERN32, K_GAUSS = 0, 1, 2
+P_FP64, P_FP32, P_MIXED = 0, 1, 2
+W_INV_GAMMA, W_PAPER_LOGRHO, W_EXPLICIT = 0, 1, 2
+KERNELS = {"exp": K_EXP, "matern32": K_MATERN32, "gauss": K_GAUSS}
+PRECISIONS = {"fp64": P_FP64, "fp32": P_FP32, "mixed": P_MIXED}
+WEIGHT_RULES = {"inv_gamma": W_INV_GAMMA, "paper_logrho": W_PAPER_LOGRHO, "explicit": W_EXPLICIT}
+PHASES = ("gather", "p2m_m2m", "m2l", "l2l_l2p", "p2p", "scatter", "matvec")
+
+# Every entry point declared in include/dwfmm.h.
+EXPORTS = ("dwfmm_plan_create", "dwfmm_plan_set_nodes", "dwfmm_tree_build", "dwfmm_matvec",
+           "dwfmm_solve", "dwfmm_plan_destroy", "dwfmm_status_string", "dwfmm_last_error",
+           "dwfmm_plan_info", "dwfmm_plan_export", "dwfmm_tree_export", "dwfmm_lists_export",
+           "dwfmm_set_profiling", "dwfmm_phase_times")
+
+
+class dwfmm_config(C.Structure):
+    _fields_ = [("d", C.c_int32), ("kernel", C.c_int32), ("sigma", C.c_double),
+                ("gamma", C.POINTER(C.c_double)), ("weight_rule", C.c_int32),
+                ("weights", C.POINTER(C.c_double)), ("q", C.c_double), ("eta", C.c_double),
+                ("leaf_size", C.c_int32), ("halton_candidates", C.c_int32),
+                ("precision", C.c_int32), ("max_rhs", C.c_int32)]
+
+
+class DwfmmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"dwfmm status {status}: {msg}")
+        self.status = status
+
+
+def load(path: str = LIB_PATH) -> C.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is not built; run paper_2402_09531_gb300.build.build()")
+    lib = C.CDLL(path)
+    P = C.c_void_p
+    i32, i64, dbl = C.c_int32, C.c_int64, C.c_double
+    pd = C.POINTER(C.c_double)
+    sig = {
+        "dwfmm_plan_create": (i32, [C.POINTER(dwfmm_config), P, C.POINTER(P)]),
+        "dwfmm_plan_set_nodes": (i32, [P, P, i64, P]),
+        "dwfmm_tree_build": (i32, [P, P, i64, i64, P]),
+        "dwfmm_matvec": (i32, [P, P, P, i32, i64, i64, P]),
+        "dwfmm_solve": (i32, [P, dbl, P, P, i32, i64, dbl, i32, C.POINTER(i32), pd, P]),
+        "dwfmm_plan_destroy": (i32, [P]),
+        "dwfmm_status_string": (C.c_char_p, [i32]),
+        "dwfmm_last_error": (C.c_char_p, [P]),
+        "dwfmm_plan_info": (i32, [P, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), C.POINTER(i32)]),
+        "dwfmm_plan_export": (i32, [P, P, P, P, P, P]),
+        "dwfmm_tree_export": (i32, [P, P, P, P, P, P]),
+        "dwfmm_lists_export": (i32, [P, P, P]),
+        "dwfmm_set_profiling": (i32, [P, i32]),
+        "dwfmm_phase_times": (i32, [P, P, P, i32]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    global _lib
+    if _lib is None:
+        _lib = load()
+    return _lib
+
+
+def _ptr(a) -> int | None:
+    """Data pointer of a torch tensor or numpy array (None for None)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            pass
+        return None
+    return getattr(stream, "cuda_stream", stream)
+
+
+class Plan:
+    """One DW-FMM plan: expansion (plan_create), tree (tree_build), matvec, solve."""
+
+    def __init__(self, d: int, kernel: str = "exp", sigma: float = 1.0, gamma=None,
+                 weight_rule: str = "inv_gamma", weights=None, q: float = 4.0, eta: float = 1.0,
+                 leaf_size: int = 64, halton_candidates: int = 0, precision: str = "fp64",
+                 max_rhs: int = 16, stream=None):
+        self._l = lib()
+        self.d = int(d)
+        self.precision = precision
+        self.max_rhs = int(max_rhs)
+        g = np.ascontiguousarray(np.ones(d) if gamma is None else np.asarray(gamma, dtype=np.float64))
+        w = None if weights is None else np.ascontiguousarray(np.asarray(weights, dtype=np.float64))
+        self._keep = (g, w)
+        cfg = dwfmm_config(self.d, KERNELS[kernel], float(sigma),
+                           g.ctypes.data_as(C.POINTER(C.c_double)),
+                           WEIGHT_RULES[weight_rule],
+                           w.ctypes.data_as(C.POINTER(C.c_double)) if w is not None else None,
+                           float(q), float(eta), int(leaf_size), int(halton_candidates),
+                           PRECISIONS[precision], self.max_rhs)
+        h = C.c_void_p()
+        st = self._l.dwfmm_plan_create(C.byref(cfg), _stream_handle(stream), C.byref(h))
+        if st != OK:
+            raise DwfmmError(st, self._l.dwfmm_status_string(st).decode())
+        self.h = h
+        self.n_x = self.info()[0]
+
+    # -- lifetime ------------------------------------------------------------
+    def close(self):
+        if getattr(self, "h", None):
+            self._l.dwfmm_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def check(self, st: int):
+        if st != OK:
+            msg = self._l.dwfmm_last_error(self.h).decode() if self.h else ""
+            raise DwfmmError(st, msg or self._l.dwfmm_status_string(st).decode())
+
+    # -- calls ---------------------------------------------------------------
+    def set_nodes(self, nodes, stream=None):
+        a = np.ascontiguousarray(np.asarray(nodes, dtype=np.float64))
+        self.check(self._l.dwfmm_plan_set_nodes(self.h, a.ctypes.data, a.shape[0], _stream_handle(stream)))
+
+    def tree_build(self, pts, stream=None):
+        """pts: (N, d) float64, torch (cuda or cpu) or numpy, row-major."""
+        n = int(pts.shape[0])
+        ld = int(pts.stride(0)) if hasattr(pts, "stride") and callable(pts.stride) else \
+            int(pts.strides[0] // 8) if n else self.d
+        self._pts_keep = pts
+        self.check(self._l.dwfmm_tree_build(self.h, _ptr(pts), n, ld, _stream_handle(stream)))
+        self.n = n
+
+    def matvec(self, x, y, stream=None):
+        """x, y: (R, N) float64 (each row one right-hand side, contiguous)."""
+        R = int(x.shape[0])
+        ldx = int(x.stride(0)) if hasattr(x, "stride") and callable(x.stride) else int(x.strides[0] // 8)
+        ldy = int(y.stride(0)) if hasattr(y, "stride") and callable(y.stride) else int(y.strides[0] // 8)
+        self.check(self._l.dwfmm_matvec(self.h, _ptr(x), _ptr(y), R, ldx, ldy, _stream_handle(stream)))
+        return y
+
+    def solve(self, lam: float, f, c, rtol: float = 1e-6, maxit: int = 1000, stream=None):
+        R = int(f.shape[0])
+        ld = int(f.stride(0)) if hasattr(f, "stride") and callable(f.stride) else int(f.strides[0] // 8)
+        it = C.c_int32(0)
+        rel = (C.c_double * R)()
+        st = self._l.dwfmm_solve(self.h, float(lam), _ptr(f), _ptr(c), R, ld, float(rtol), int(maxit),
+                                 C.byref(it), rel, _stream_handle(stream))
+        return st, int(it.value), [float(v) for v in rel]
+
+    def info(self):
+        nx, nf, nn, dep = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int32()
+        self.check(self._l.dwfmm_plan_info(self.h, C.byref(nx), C.byref(nf), C.byref(nn), C.byref(dep)))
+        return int(nx.value), int(nf.value), int(nn.value), int(dep.value)
+
+    def export_expansion(self):
+        n, d = self.n_x, self.d
+        w = np.zeros(d)
+        lam = np.zeros((n, d), dtype=np.int32)
+        nodes = np.zeros((n, d))
+        piv = np.zeros(n, dtype=np.int32)
+        vinv = np.zeros((n, n))
+        self.check(self._l.dwfmm_plan_export(self.h, w.ctypes.data, lam.ctypes.data, nodes.ctypes.data,
+                                             piv.ctypes.data, vinv.ctypes.data))
+        return dict(weights=w, lam=lam, nodes=nodes, pivots=piv, vinv=vinv)
+
+    def export_tree(self):
+        _, _, _, J = self.info()
+        nc = (1 << (J + 1)) - 1
+        perm = np.zeros(self.n, dtype=np.int64)
+        b = np.zeros(nc, dtype=np.int64)
+        e = np.zeros(nc, dtype=np.int64)
+        lo = np.zeros((nc, self.d))
+        hi = np.zeros((nc, self.d))
+        self.check(self._l.dwfmm_tree_export(self.h, perm.ctypes.data, b.ctypes.data, e.ctypes.data,
+                                             lo.ctypes.data, hi.ctypes.data))
+        return dict(depth=J, perm=perm, begin=b, end=e, lo=lo, hi=hi)
+
+    def export_lists(self):
+        _, nf, nn, _ = self.info()
+        far = np.zeros((nf, 2), dtype=np.int32)
+        near = np.zeros((nn, 2), dtype=np.int32)
+        self.check(self._l.dwfmm_lists_export(self.h, far.ctypes.data, near.ctypes.data))
+        return far, near
+
+    def set_profiling(self, on: bool):
+        self.check(self._l.dwfmm_set_profiling(self.h, 1 if on else 0))
+
+    def phase_times(self, reset: bool = True):
+        ms = np.zeros(7)
+        ln = np.zeros(7, dtype=np.int64)
+        self.check(self._l.dwfmm_phase_times(self.h, ms.ctypes.data, ln.ctypes.data, 1 if reset else 0))
+        return {p: (float(ms[i]), int(ln[i])) for i, p in enumerate(PHASES)}
