@@ -1,0 +1,384 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 DW-FMM matvec (one JSON line on rank 0).
+
+A step is one DW-FMM matvec y = K_tilde x (gather, P2M, M2M, M2L, L2L, L2P,
+P2P, scatter) over one batch of R right-hand sides on a resident tree; the
+expansion setup (weights, index set, nodes, V^{-1}) and the tree build
+(tree, lists, cluster data) are timed separately and reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the float64 CPU oracle on the same workload (a
+bounded sample per step: the rows of one target leaf, with the full upward
+pass).  Under torchrun each rank runs an independent replica (the method
+runs on one GPU; replicas scale weakly); rank 0 prints.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "DW-FMM matvec pts·RHS/s and CG solve p50/p99 ms, mixed vs FP64 @ rel err 1e-6"
+UNIT = "pts·RHS/s"
+SMS = 152
+FP32_LANES = 128
+
+
+def workload(name: str):
+    import dwfmm_inputs as di
+    table = {"mixed": di.mixed_gauss_d10, "fp64": di.fp64_matern_d8, "small": di.small_exp_d4}
+    return table[name]()
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except Exception:
+        return {}
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except Exception:
+                self.p.kill()
+                self.out = ""
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle sample (runs in its own single-threaded process)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(name: str, steps: int, warmup: int, leaf_index: int = 0):
+    """Time the float64 oracle's matvec restricted to one target leaf (full
+    upward pass, far field of the leaf's ancestors, near field).  Tree-only
+    matrices are built before timing (they are setup, as on the GPU)."""
+    import numpy as np
+    import dwfmm_inputs as di
+    from oracle import dwfmm_oracle as o
+    w = workload(name)
+    X, f = di.sites_and_rhs(w)
+    t0 = time.time()
+    pb = o.make_problem(X, w.kernel, o.weights_inv_gamma(w.gamma), w.q, w.leaf, w.eta, w.sigma)
+    first = (1 << pb.tree.depth) - 1
+    leaf = first + leaf_index
+    anc, c = [], leaf
+    while True:
+        anc.append(c)
+        if c == 0:
+            break
+        c = (c - 1) // 2
+    for c in range(1, pb.tree.nclusters):
+        o.problem_transfer(pb, c)
+    for lvl in pb.lists.far:
+        for (t, s) in lvl:
+            if int(t) in anc:
+                o.problem_coefficient(pb, int(t), int(s))
+    setup_s = time.time() - t0
+    times = []
+    for k in range(warmup + steps):
+        t = time.perf_counter()
+        o.fmm_matvec_leaves(pb, f, [leaf])
+        if k >= warmup:
+            times.append(time.perf_counter() - t)
+    rows = int(pb.tree.end[leaf] - pb.tree.begin[leaf])
+    units = rows * w.nrhs
+    return {"units_per_step": units, "s_per_step": statistics.mean(times), "steps": steps,
+            "setup_s": setup_s, "rows": rows, "leaf": leaf}
+
+
+def start_oracle_subprocess(name: str, steps: int, warmup: int):
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[v] = "1"
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-sample", name, "--steps", str(steps),
+           "--warmup", str(warmup)]
+    return subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env)
+
+
+def finish_oracle_subprocess(p, timeout: float = 600.0):
+    try:
+        out, err = p.communicate(timeout=timeout)
+    except subprocess.TimeoutExpired:
+        p.kill()
+        return None
+    for line in out.splitlines()[::-1]:
+        line = line.strip()
+        if line.startswith("{"):
+            return json.loads(line)
+    return None
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def near_pairs(plan) -> int:
+    import numpy as np
+    t = plan.export_tree()
+    _, near = plan.export_lists()
+    size = (t["end"] - t["begin"]).astype(np.int64)
+    return int(np.sum(size[near[:, 0]] * size[near[:, 1]]))
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    cpu_proc = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu_proc = start_oracle_subprocess(args.workload, args.cpu_steps, 1)
+
+    import __graft_entry__ as ge
+    ge.build()
+    import dwfmm_inputs as di
+    from paper_2402_09531_gb300 import Plan
+
+    w = workload(args.workload)
+    if args.n:
+        import dwfmm_inputs as di
+        w = di.scaled(w, args.n)
+    w.seed = w.seed + 1000 * rank          # independent replica per rank
+    X, f = di.sites_and_rhs(w)
+    N, R, d = w.n, w.nrhs, w.d
+    stream = torch.cuda.current_stream(dev)
+
+    t0 = time.perf_counter()
+    plan = Plan(d=d, kernel=w.kernel, sigma=w.sigma, gamma=w.gamma, q=w.q, eta=w.eta,
+                leaf_size=w.leaf, precision=args.precision, max_rhs=R)
+    setup_ms = (time.perf_counter() - t0) * 1e3
+    Xd = torch.from_numpy(X).to(dev)
+    torch.cuda.synchronize()
+    tree_ms = []
+    for _ in range(2):
+        t0 = time.perf_counter()
+        plan.tree_build(Xd)
+        torch.cuda.synchronize()
+        tree_ms.append((time.perf_counter() - t0) * 1e3)
+    n_x, n_far, n_near, depth = plan.info()
+    pairs = near_pairs(plan)
+
+    xd = torch.from_numpy(f).to(dev)
+    yd = torch.empty_like(xd)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        plan.matvec(xd, yd)
+    torch.cuda.synchronize()
+
+    plan.set_profiling(True)
+    plan.phase_times(reset=True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()                      # evict L2 (129 MB) between steps
+            ev[k][0].record(stream)
+            plan.matvec(xd, yd)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    phases = plan.phase_times(reset=True)
+    # per-phase times with every phase alone on the GPU (not part of the value)
+    plan.set_profiling(True, serialize=True)
+    for _ in range(2):
+        plan.matvec(xd, yd)
+    iso = plan.phase_times(reset=True)
+    plan.set_profiling(False)
+    ms = statistics.mean(step_ms)
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_max = total_ms / args.steps
+    value = world * N * R / (ms_max / 1e3)
+
+    # e2e through the public API with host buffers (pinned), copies inside
+    xh = torch.from_numpy(f).pin_memory()
+    yh = torch.empty_like(xh).pin_memory()
+    for _ in range(2):
+        plan.matvec(xh, yh)
+    e2e_s = []
+    with ClockSampler(local) as clk2:
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            plan.matvec(xh, yh)               # synchronises (host y)
+            e2e_s.append(time.perf_counter() - t0)
+    e2e_t = statistics.mean(e2e_s)
+    if dist:
+        t = torch.tensor([e2e_t], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_t = float(t.item())
+
+    # roofline of the dominant kernel (P2P): algorithmic FP32 flops per launch
+    p2p_ms, p2p_launches = phases["p2p"]
+    p2p_avg_ms = p2p_ms / max(1, p2p_launches)
+    flops_pair = 3 * d + 4 + 2 * R
+    achieved = pairs * flops_pair / (p2p_avg_ms / 1e3) / 1e12
+    peaks = measured_peaks()
+    clock_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = SMS * FP32_LANES * 2 * clock_mhz * 1e6 / 1e12
+    launches = sum(v[1] for k, v in phases.items() if k != "matvec")
+
+    cpu = None
+    if cpu_proc is not None:
+        res = finish_oracle_subprocess(cpu_proc)
+        if res:
+            cpu = {"value": res["units_per_step"] / res["s_per_step"], "unit": UNIT, "cores": 1,
+                   "kind": "oracle",
+                   "sample": (f"float64 numpy oracle, one target leaf ({res['rows']} rows x {R} RHS) of "
+                              f"the same workload per step: full upward pass, far field of the leaf's "
+                              f"ancestors, near field; tree-only matrices built before timing "
+                              f"({res['setup_s']:.0f} s); mean of {res['steps']} steps, 1 thread")}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision != "fp64" else "f64",
+            "data": "synthetic (uniform sites in prod_k [-gamma_k, gamma_k], N(0,1) right-hand sides)",
+            "config": {"workload": w.name, "d": d, "N": N, "nrhs": R, "kernel": w.kernel, "q": w.q,
+                       "weights": "omega_k = gamma_1/gamma_k", "n_x": n_x, "leaf": w.leaf, "eta": w.eta,
+                       "depth": depth, "far_blocks": n_far, "near_blocks": n_near, "near_pairs": pairs,
+                       "precision": args.precision, "parallelism": f"replicas x{world}",
+                       "l2": "flushed between steps (512 MiB write)"},
+            "e2e": {"value": world * N * R / e2e_t, "unit": UNIT, "h2d_bytes_per_step": int(xh.numel() * 8),
+                    "d2h_bytes_per_step": int(yh.numel() * 8)},
+            "gpu_launches": int(launches),
+            "roofline": {"kernel": "p2p (near field)", "bound": "alu", "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "flops_per_pair": flops_pair, "pairs_per_launch": pairs,
+                         "launch_ms": p2p_avg_ms,
+                         "peak_basis": f"{SMS} SMs x {FP32_LANES} FP32 lanes x 2 flop x {clock_mhz:.0f} MHz"},
+            "phase_ms_per_step": {k: v[0] / args.steps for k, v in phases.items()},
+            "phase_ms_isolated": {k: v[0] / 2 for k, v in iso.items()},
+            "setup_ms": setup_ms, "tree_build_ms": min(tree_ms),
+            "clocks": clk.summary(), "clocks_e2e": clk2.summary(),
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    res = oracle_sample(args.workload, args.steps, args.warmup)
+    w = workload(args.workload)
+    value = res["units_per_step"] / res["s_per_step"]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["s_per_step"] * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (uniform sites in prod_k [-gamma_k, gamma_k], N(0,1) right-hand sides)",
+        "impl": "reference",
+        "config": {"workload": w.name, "d": w.d, "N": w.n, "nrhs": w.nrhs, "kernel": w.kernel, "q": w.q,
+                   "leaf": w.leaf, "eta": w.eta},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"one target leaf ({res['rows']} rows x {w.nrhs} RHS) per step, full "
+                                   f"upward pass; tree-only matrices built before timing"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="mixed", choices=["mixed", "fp64", "small"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "fp32", "mixed"])
+    ap.add_argument("--cpu-steps", type=int, default=2)
+    ap.add_argument("--n", type=int, default=0, help="override N (smaller case for profiling)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-sample", default=None)
+    args = ap.parse_args()
+    if args.oracle_sample:
+        print(json.dumps(oracle_sample(args.oracle_sample, args.steps, args.warmup)), flush=True)
+        return
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -190,7 +190,10 @@ dwfmm_status dwfmm_tree_export(dwfmm_plan plan, int64_t* perm, int64_t* begin, i
 dwfmm_status dwfmm_lists_export(dwfmm_plan plan, int32_t* far, int32_t* near);
 
 /* Phase timing.  With enable != 0 every later matvec records CUDA events on
- * the streams that launch each phase; dwfmm_phase_times returns, per phase,
+ * the streams that launch each phase (enable = 1: the near field still runs
+ * on its own stream, concurrently with the far field, as in production;
+ * enable = 2: the near field runs on the caller's stream after the far field,
+ * so each phase is timed alone).  dwfmm_phase_times returns, per phase,
  * the summed milliseconds since the last reset and the launch counts:
  * ms[0] gather, [1] P2M+M2M, [2] M2L, [3] L2L+L2P, [4] P2P, [5] scatter,
  * [6] whole matvec; launches[i] the number of kernel launches of phase i.

@@ -25,7 +25,7 @@ claims of Sec. 6.1 are pinned instead).
 from __future__ import annotations
 
 import math
-from dataclasses import dataclass
+from dataclasses import dataclass, field
 
 import numpy as np
 
@@ -405,34 +405,50 @@ class Lists:
     near: np.ndarray
 
 
+def admissible_pairs(lo: np.ndarray, hi: np.ndarray, t: np.ndarray, s: np.ndarray,
+                     eta: float) -> np.ndarray:
+    """Eq. (5.1) for many pairs at once, with the same float64 operations in
+    the same order as `admissible` (products and adds over k, no fused
+    multiply-add), so both give identical decisions."""
+    D2 = np.zeros(t.size)
+    da = np.zeros(t.size)
+    db = np.zeros(t.size)
+    for k in range(lo.shape[1]):
+        g = np.maximum(0.0, np.maximum(lo[s, k] - hi[t, k], lo[t, k] - hi[s, k]))
+        D2 = D2 + g * g
+        ea = hi[t, k] - lo[t, k]
+        eb = hi[s, k] - lo[s, k]
+        da = da + ea * ea
+        db = db + eb * eb
+    return (D2 > 0.0) & (D2 >= (eta * eta) * np.maximum(da, db))
+
+
 def build_lists(tree: Tree, eta: float) -> Lists:
     """Level-wise block-cluster tree traversal (Sec. 5.2).
 
     Reading of the garbled farfield definition: nu x nu' is in F iff it is
     admissible and parent(nu) x parent(nu') is not; N holds the leaf pairs
     that are not admissible.  Both orderings (nu, nu') and (nu', nu) are kept.
+    Candidates of one level are tested together (`admissible_pairs`).
     """
     J = tree.depth
     far = [np.zeros((0, 2), dtype=np.int64) for _ in range(J + 1)]
     near = np.zeros((0, 2), dtype=np.int64)
     if tree.n == 0:
         return Lists(far, near)
-    cand = [(0, 0)]
+    ct = np.array([0], dtype=np.int64)
+    cs = np.array([0], dtype=np.int64)
     for j in range(J + 1):
-        f, nxt, nr = [], [], []
-        for (t, s) in sorted(cand):
-            if admissible(tree.lo[t], tree.hi[t], tree.lo[s], tree.hi[s], eta):
-                f.append((t, s))
-            elif j < J:
-                for a in (1, 2):
-                    for b in (1, 2):
-                        nxt.append((2 * t + a, 2 * s + b))
-            else:
-                nr.append((t, s))
-        far[j] = np.array(f, dtype=np.int64).reshape(-1, 2)
+        order = np.lexsort((cs, ct))
+        ct, cs = ct[order], cs[order]
+        adm = admissible_pairs(tree.lo, tree.hi, ct, cs, eta)
+        far[j] = np.stack([ct[adm], cs[adm]], axis=1)
+        nt, ns = ct[~adm], cs[~adm]
         if j == J:
-            near = np.array(nr, dtype=np.int64).reshape(-1, 2)
-        cand = nxt
+            near = np.stack([nt, ns], axis=1)
+            break
+        ct = np.concatenate([2 * nt + a for a in (1, 2) for b in (1, 2)])
+        cs = np.concatenate([2 * ns + b for a in (1, 2) for b in (1, 2)])
     return Lists(far, near)
 
 
@@ -479,13 +495,33 @@ def coefficient_matrix(exp_: Expansion, S: np.ndarray) -> np.ndarray:
 
 @dataclass
 class Problem:
-    """Sites, kernel and the structures the FMM needs."""
+    """Sites, kernel and the structures the FMM needs.  `cache` memoizes the
+    matrices that depend on the tree only (T_c and C_{t,s}), so repeated
+    matvecs on one tree do not recompute them; the arithmetic is unchanged."""
     X: np.ndarray
     kernel: str
     sigma: float
     exp_: Expansion
     tree: Tree
     lists: Lists
+    cache: dict = field(default_factory=dict)
+
+
+def problem_transfer(pb: Problem, c: int) -> np.ndarray:
+    """T_c of Sec. 5.2 for this problem's tree (memoized)."""
+    key = ("T", c)
+    if key not in pb.cache:
+        pb.cache[key] = transfer_matrix(pb.exp_, pb.tree, c)
+    return pb.cache[key]
+
+
+def problem_coefficient(pb: Problem, t: int, s: int) -> np.ndarray:
+    """C_{t,s} = V^{-1} S_{t,s} V^{-T} for this problem's tree (memoized)."""
+    key = ("C", t, s)
+    if key not in pb.cache:
+        S = coupling_matrix(pb.exp_, pb.tree, t, s, pb.kernel, pb.sigma)
+        pb.cache[key] = coefficient_matrix(pb.exp_, S)
+    return pb.cache[key]
 
 
 def make_problem(X, kernel: str, weights, q: float, leaf: int, eta: float,
@@ -513,7 +549,7 @@ def upward_pass(pb: Problem, xt: np.ndarray) -> dict:
         for c in range(f, l):
             acc = 0.0
             for ch in (2 * c + 1, 2 * c + 2):
-                acc = acc + transfer_matrix(pb.exp_, tr, ch).T @ mu[ch]
+                acc = acc + problem_transfer(pb, ch).T @ mu[ch]
             mu[c] = acc
     return mu
 
@@ -527,9 +563,7 @@ def farfield_coefficients(pb: Problem, mu: dict, targets=None) -> dict:
             t, s = int(t), int(s)
             if targets is not None and t not in targets:
                 continue
-            S = coupling_matrix(pb.exp_, pb.tree, t, s, pb.kernel, pb.sigma)
-            C = coefficient_matrix(pb.exp_, S)
-            lam[t] = lam.get(t, 0.0) + C @ mu[s]
+            lam[t] = lam.get(t, 0.0) + problem_coefficient(pb, t, s) @ mu[s]
     return lam
 
 
@@ -555,7 +589,7 @@ def downward_pass(pb: Problem, lam: dict, R: int, leaves=None) -> dict:
                 continue
             v = np.zeros((n, R)) + lam.get(c, 0.0)
             if c > 0:
-                v = v + transfer_matrix(pb.exp_, tr, c) @ acc[(c - 1) // 2]
+                v = v + problem_transfer(pb, c) @ acc[(c - 1) // 2]
             acc[c] = v
     f, l = tr.level_range(tr.depth)
     return {c: acc[c] for c in range(f, l) if c in acc}

@@ -60,6 +60,20 @@ void Plan::free_tree() {
   cg_dot.release();
   cg_tmp.release();
   scratch.release();
+  d_ptsk.release();
+  d_ynodek.release();
+  dpad = -1;
+}
+
+// Report a bounded device wait that gave up (raised by the tuned kernels).
+void check_device_error(Plan& P) {
+  if (!P.d_err.p) return;
+  int e = 0;
+  DW_CUDA(cudaMemcpy(&e, P.d_err.p, sizeof(int), cudaMemcpyDeviceToHost));
+  if (e) {
+    DW_CUDA(cudaMemset(P.d_err.p, 0, sizeof(int)));
+    fail(DWFMM_ERR_TIMEOUT, "a bounded wait on a shared-memory copy gave up");
+  }
 }
 
 void Plan::free_all() {
@@ -71,6 +85,7 @@ void Plan::free_all() {
   d_nodes.release();
   d_vinv.release();
   d_vinv32.release();
+  d_err.release();
   stage_in.release();
   stage_out.release();
   for (auto& r : tm.recs) {
@@ -80,6 +95,8 @@ void Plan::free_all() {
   tm.recs.clear();
   if (ev_fork) cudaEventDestroy(ev_fork);
   if (ev_join) cudaEventDestroy(ev_join);
+  if (ev_scaled) cudaEventDestroy(ev_scaled);
+  ev_scaled = nullptr;
   if (side) cudaStreamDestroy(side);
   ev_fork = ev_join = nullptr;
   side = nullptr;
@@ -184,6 +201,9 @@ dwfmm_status dwfmm_plan_create(const dwfmm_config* cfg, void* stream, dwfmm_plan
     DW_CUDA(cudaStreamCreateWithFlags(&P.side, cudaStreamNonBlocking));
     DW_CUDA(cudaEventCreateWithFlags(&P.ev_fork, cudaEventDisableTiming));
     DW_CUDA(cudaEventCreateWithFlags(&P.ev_join, cudaEventDisableTiming));
+    DW_CUDA(cudaEventCreateWithFlags(&P.ev_scaled, cudaEventDisableTiming));
+    P.d_err.alloc(1);
+    DW_CUDA(cudaMemset(P.d_err.p, 0, sizeof(int)));
     dw::setup_expansion(P);
     if (dw::farfield_smem_need(P, true) > 220 * 1024)
       fail(DWFMM_ERR_INVALID_ARG, "index set too large for the far-field kernels");
@@ -270,6 +290,7 @@ dwfmm_status dwfmm_matvec(dwfmm_plan plan, const double* x, double* y, int32_t n
       DW_CUDA(cudaMemcpy2DAsync(y, ldy * sizeof(double), yd, P.N * sizeof(double), P.N * sizeof(double),
                                 nrhs, cudaMemcpyDeviceToHost, P.stream));
       DW_CUDA(cudaStreamSynchronize(P.stream));
+      dw::check_device_error(P);
     }
     DW_CUDA(cudaGetLastError());
     return DWFMM_OK;
@@ -327,6 +348,7 @@ dwfmm_status dwfmm_solve(dwfmm_plan plan, double lambda, const double* f, double
       DW_CUDA(cudaMemcpy2DAsync(c, ld * sizeof(double), cs.p, P.N * sizeof(double), P.N * sizeof(double),
                                 nrhs, cudaMemcpyDeviceToHost, P.stream));
     DW_CUDA(cudaStreamSynchronize(P.stream));
+    dw::check_device_error(P);
     if (iters_out) *iters_out = its;
     if (s != DWFMM_OK) P.last_error = dwfmm_status_string(s);
     return s;
@@ -409,6 +431,7 @@ dwfmm_status dwfmm_lists_export(dwfmm_plan plan, int32_t* far, int32_t* near) {
 dwfmm_status dwfmm_set_profiling(dwfmm_plan plan, int32_t enable) {
   if (!plan) return DWFMM_ERR_INVALID_ARG;
   plan->P.tm.on = enable != 0;
+  plan->P.tm.serialize = enable == 2;
   return DWFMM_OK;
 }
 
@@ -417,6 +440,7 @@ dwfmm_status dwfmm_phase_times(dwfmm_plan plan, double* ms, int64_t* launches, i
   Plan& P = plan->P;
   return guarded(&P, [&]() -> dwfmm_status {
     dw::timers_collect(P);
+    dw::check_device_error(P);
     for (int i = 0; i < 7; ++i) {
       if (ms) ms[i] = P.tm.ms[i];
       if (launches) launches[i] = P.tm.launches[i];

@@ -117,6 +117,7 @@ struct TimerRec {
 
 struct Timers {
   bool on = false;
+  bool serialize = false;
   std::vector<cudaEvent_t> open;
   std::vector<TimerRec> recs;
   double ms[8] = {0};
@@ -177,6 +178,12 @@ struct Plan {
   // scratch for tree build
   DBuf<unsigned char> scratch;
 
+  // tuned float32 kernel summation: scaled blocks [g][dpad+1][ld]
+  int dpad = -1;
+  DBuf<float> d_ptsk, d_ynodek;
+  cudaEvent_t ev_scaled = nullptr;
+  DBuf<int> d_err;   // device error flag (3 = a bounded wait timed out)
+
   Timers tm;
 
   ExpDev exp_dev() const {
@@ -207,6 +214,9 @@ void launch_scatter(Plan& P, double* y, int64_t ldy, int r0, int Rc, bool fp64);
 void launch_farfield(Plan& P, int Rc, bool fp64);
 void launch_m2l(Plan& P, int Rc, bool fp64);
 void launch_nearfield(Plan& P, int Rc, bool fp64, cudaStream_t s);
+bool p2p_f32_tuned(Plan& P, int Rc, cudaStream_t s);
+bool m2l_f32_tuned(Plan& P, int Rc);
+void check_device_error(Plan& P);
 
 // ---- solve (solve.cu) ----
 dwfmm_status solve(Plan& P, double lambda, const double* f, double* c, int R, int64_t ld,

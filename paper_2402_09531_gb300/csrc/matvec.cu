@@ -71,14 +71,21 @@ void matvec_device(Plan& P, const double* x, int64_t ldx, double* y, int64_t ldy
     timer_begin(P, 0, s);
     launch_gather(P, x, ldx, r0, Rc, fp64);
     timer_end(P, 0, s, 1);
-    DW_CUDA(cudaEventRecord(P.ev_fork, s));
-    DW_CUDA(cudaStreamWaitEvent(P.side, P.ev_fork, 0));
-    timer_begin(P, 4, P.side);
-    launch_nearfield(P, Rc, fp64, P.side);
-    timer_end(P, 4, P.side, 1);
-    DW_CUDA(cudaEventRecord(P.ev_join, P.side));
-    launch_farfield(P, Rc, fp64);
-    DW_CUDA(cudaStreamWaitEvent(s, P.ev_join, 0));
+    if (P.tm.on && P.tm.serialize) {  // every phase alone on the caller's stream
+      launch_farfield(P, Rc, fp64);
+      timer_begin(P, 4, s);
+      launch_nearfield(P, Rc, fp64, s);
+      timer_end(P, 4, s, 1);
+    } else {
+      DW_CUDA(cudaEventRecord(P.ev_fork, s));
+      DW_CUDA(cudaStreamWaitEvent(P.side, P.ev_fork, 0));
+      timer_begin(P, 4, P.side);
+      launch_nearfield(P, Rc, fp64, P.side);
+      timer_end(P, 4, P.side, 1);
+      DW_CUDA(cudaEventRecord(P.ev_join, P.side));
+      launch_farfield(P, Rc, fp64);
+      DW_CUDA(cudaStreamWaitEvent(s, P.ev_join, 0));
+    }
     timer_begin(P, 5, s);
     launch_scatter(P, y, ldy, r0, Rc, fp64);
     timer_end(P, 5, s, 1);

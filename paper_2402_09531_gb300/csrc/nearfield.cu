@@ -143,12 +143,10 @@ void p2p_impl(Plan& P, int Rc, const T* pts, const T* xb, T* ynear, cudaStream_t
 
 }  // namespace
 
-bool p2p_f32_tuned(Plan& P, int Rc, cudaStream_t s);
-
 void launch_m2l(Plan& P, int Rc, bool fp64) {
   if (P.jmin > P.J) return;
   if (fp64) m2l_impl<double>(P, Rc, P.d_ynode64.p, P.mom64.p, P.loc64.p);
-  else m2l_impl<float>(P, Rc, P.d_ynode32.p, P.mom32.p, P.loc32.p);
+  else if (!m2l_f32_tuned(P, Rc)) m2l_impl<float>(P, Rc, P.d_ynode32.p, P.mom32.p, P.loc32.p);
   DW_CUDA(cudaGetLastError());
 }
 

@@ -1,15 +1,462 @@
-// Tuned float32 P2P (near field) for sm_103a.
+// Tuned float32 kernel summation for sm_103a: the P2P near field and the M2L
+// couplings of the DW-FMM (Sec. 5.2), y_i = sum_j phi(|x_i - x_j| / sigma) q_j.
+//
+// Design (one CTA per target group: a leaf, or a cluster's node set):
+//  - Source blocks (scaled coordinates plus a norm row, then R charge rows)
+//    are contiguous and 32-byte aligned in HBM, so each block is two 1-D TMA
+//    bulk copies (cp.async.bulk, mbarrier completion) into a double-buffered
+//    shared-memory stage; thread 0 issues, every thread waits with a bounded
+//    try_wait loop that raises an error flag instead of hanging.
+//  - Each thread owns TT targets; sources are read as float4 broadcasts from
+//    shared memory, 4 sources per step.
+//  - The kernel constants are folded into the coordinates when the source
+//    blocks are built:
+//      Gaussian:  x' = x sqrt(log2 e / (2 sigma^2)),  phi = ex2(2 x'.s' - |x'|^2 - |s'|^2)
+//      exp:       x' = x log2 e / sigma,               phi = ex2(-|x' - s'|)
+//      Matern:    x' = x sqrt3 / sigma,                phi = (1 + r') ex2(-r' log2 e)
+//    so the Gaussian costs D FMAs, one add and one MUFU.EX2 per pair.
+//  - Per source block the contributions are summed in float32 partials, then
+//    folded into per-target running sums with Kahan compensation.
+#include <cstdint>
+
 #include "dwfmm_internal.cuh"
 
 namespace dw {
 
-// Returns false when no tuned kernel covers this shape; the generic kernel
-// of nearfield.cu then runs.
-bool p2p_f32_tuned(Plan& P, int Rc, cudaStream_t s) {
-  (void)P;
-  (void)Rc;
-  (void)s;
+namespace {
+
+constexpr int kThreadsMax = 128;
+constexpr int kTT = 2;
+constexpr long long kWaitLimit = 1ll << 24;   // ~ seconds of polling: a copy never takes that long
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// Bounded wait for phase `parity` of the barrier; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_addr(bar);
+  for (long long it = 0; it < kWaitLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
   return false;
+}
+
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+struct SumArgs {
+  const float* tgt;        // target blocks [g][D+1][ld] (scaled coords, norm row)
+  int64_t tgt_gstride;
+  const float* src;        // source blocks [g][D+1][ld]
+  int64_t src_gstride;
+  const float* q;          // charges [g][kRC][ld] (row r0 applied)
+  int64_t q_gstride;
+  float* out;              // [g][kRC][ld] (row r0 applied)
+  int64_t out_gstride;
+  const int32_t* rowptr;   // CSR over target groups (indexed by first + blockIdx.x)
+  const int32_t* col;      // source group ids
+  const int32_t* count;    // group sizes (count[count_off + g]); nullptr -> count_const
+  int count_off;
+  int count_const;
+  int first;               // first target group
+  int ld;                  // m_pad or n_pad (multiple of 8)
+  int Rc;                  // right-hand sides actually written (<= RC)
+  int* err;
+};
+
+template <int KER>
+__device__ __forceinline__ float phi_scaled(float a) {
+  // a = the kernel's argument after scaling: Gaussian: exponent; exp/Matern: r'^2
+  if (KER == DWFMM_K_GAUSS) return ex2_approx(a);
+  const float r = sqrt_approx(a);
+  if (KER == DWFMM_K_EXP) return ex2_approx(-r);
+  const float e = ex2_approx(-1.4426950408889634f * r);
+  return fmaf(r, e, e);
+}
+
+template <int D, int RC, int KER>
+__global__ void __launch_bounds__(kThreadsMax, 3) k_sum_f32(SumArgs a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t full[2];
+  const int ld = a.ld;
+  const int stage_floats = (D + 1) * ld + RC * ld;
+  float* stage0 = reinterpret_cast<float*>(smem);
+  const int g = a.first + blockIdx.x;
+  const int rb = a.rowptr[g], re = a.rowptr[g + 1];
+  const uint32_t coord_bytes = static_cast<uint32_t>((D + 1) * ld * sizeof(float));
+  const uint32_t q_bytes = static_cast<uint32_t>(RC * ld * sizeof(float));
+
+  if (threadIdx.x == 0) {
+    mbar_init(&full[0], 1);
+    mbar_init(&full[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  // tiles are numbered across all target passes: stage = tile & 1,
+  // completion parity of that stage's barrier = (tile >> 1) & 1
+  int tile_base = 0;
+  auto issue = [&](int e, int tile) {
+    const int s = a.col[e];
+    float* st = stage0 + (tile & 1) * stage_floats;
+    uint64_t* bar = &full[tile & 1];
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(bar, coord_bytes + q_bytes);
+    bulk_copy(st, a.src + s * a.src_gstride, coord_bytes, bar);
+    bulk_copy(st + (D + 1) * ld, a.q + s * a.q_gstride, q_bytes, bar);
+  };
+
+  for (int tb = 0; tb < ld; tb += kTT * blockDim.x) {
+    // targets of this thread
+    float xt[kTT][D];
+    float nt[kTT];
+    int ti[kTT];
+#pragma unroll
+    for (int t = 0; t < kTT; ++t) {
+      ti[t] = tb + threadIdx.x + t * blockDim.x;
+      const int i = ti[t] < ld ? ti[t] : 0;
+      const float* tp = a.tgt + g * a.tgt_gstride + i;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const float v = tp[k * ld];
+        xt[t][k] = (KER == DWFMM_K_GAUSS) ? 2.0f * v : v;
+      }
+      nt[t] = (KER == DWFMM_K_GAUSS) ? tp[D * ld] : 0.0f;
+    }
+    float acc[kTT][RC], comp[kTT][RC];
+#pragma unroll
+    for (int t = 0; t < kTT; ++t)
+#pragma unroll
+      for (int r = 0; r < RC; ++r) {
+        acc[t][r] = 0.0f;
+        comp[t][r] = 0.0f;
+      }
+
+    if (threadIdx.x == 0) {
+      if (rb < re) issue(rb, tile_base);
+      if (rb + 1 < re) issue(rb + 1, tile_base + 1);
+    }
+    bool timeout = false;
+    for (int e = rb; e < re; ++e) {
+      const int tile = tile_base + (e - rb);
+      const int sidx = tile & 1;
+      const uint32_t parity = static_cast<uint32_t>((tile >> 1) & 1);
+      if (!mbar_wait(&full[sidx], parity)) timeout = true;
+      const float* sc = stage0 + sidx * stage_floats;
+      const float* sq = sc + (D + 1) * ld;
+      const int scnt = a.count ? a.count[a.count_off + a.col[e]] : a.count_const;
+      const int s4 = timeout ? 0 : ((scnt + 3) & ~3);
+      float part[kTT][RC];
+#pragma unroll
+      for (int t = 0; t < kTT; ++t)
+#pragma unroll
+        for (int r = 0; r < RC; ++r) part[t][r] = 0.0f;
+      for (int j = 0; j < s4; j += 4) {
+        float ph[kTT][4];
+        if (KER == DWFMM_K_GAUSS) {
+          const float4 ns = *reinterpret_cast<const float4*>(sc + D * ld + j);
+#pragma unroll
+          for (int t = 0; t < kTT; ++t) {
+            ph[t][0] = -(nt[t] + ns.x);
+            ph[t][1] = -(nt[t] + ns.y);
+            ph[t][2] = -(nt[t] + ns.z);
+            ph[t][3] = -(nt[t] + ns.w);
+          }
+#pragma unroll
+          for (int k = 0; k < D; ++k) {
+            const float4 s = *reinterpret_cast<const float4*>(sc + k * ld + j);
+#pragma unroll
+            for (int t = 0; t < kTT; ++t) {
+              ph[t][0] = fmaf(xt[t][k], s.x, ph[t][0]);
+              ph[t][1] = fmaf(xt[t][k], s.y, ph[t][1]);
+              ph[t][2] = fmaf(xt[t][k], s.z, ph[t][2]);
+              ph[t][3] = fmaf(xt[t][k], s.w, ph[t][3]);
+            }
+          }
+        } else {
+#pragma unroll
+          for (int t = 0; t < kTT; ++t) ph[t][0] = ph[t][1] = ph[t][2] = ph[t][3] = 0.0f;
+#pragma unroll
+          for (int k = 0; k < D; ++k) {
+            const float4 s = *reinterpret_cast<const float4*>(sc + k * ld + j);
+#pragma unroll
+            for (int t = 0; t < kTT; ++t) {
+              float df = xt[t][k] - s.x;
+              ph[t][0] = fmaf(df, df, ph[t][0]);
+              df = xt[t][k] - s.y;
+              ph[t][1] = fmaf(df, df, ph[t][1]);
+              df = xt[t][k] - s.z;
+              ph[t][2] = fmaf(df, df, ph[t][2]);
+              df = xt[t][k] - s.w;
+              ph[t][3] = fmaf(df, df, ph[t][3]);
+            }
+          }
+        }
+#pragma unroll
+        for (int t = 0; t < kTT; ++t)
+#pragma unroll
+          for (int u = 0; u < 4; ++u) ph[t][u] = phi_scaled<KER>(ph[t][u]);
+#pragma unroll
+        for (int r = 0; r < RC; ++r) {
+          const float4 qv = *reinterpret_cast<const float4*>(sq + r * ld + j);
+#pragma unroll
+          for (int t = 0; t < kTT; ++t) {
+            float p = part[t][r];
+            p = fmaf(ph[t][0], qv.x, p);
+            p = fmaf(ph[t][1], qv.y, p);
+            p = fmaf(ph[t][2], qv.z, p);
+            p = fmaf(ph[t][3], qv.w, p);
+            part[t][r] = p;
+          }
+        }
+      }
+      // Kahan: acc += part
+#pragma unroll
+      for (int t = 0; t < kTT; ++t)
+#pragma unroll
+        for (int r = 0; r < RC; ++r) {
+          const float y = part[t][r] - comp[t][r];
+          const float s = acc[t][r] + y;
+          comp[t][r] = (s - acc[t][r]) - y;
+          acc[t][r] = s;
+        }
+      // every thread is done with this stage before it is refilled
+      if (__syncthreads_or(timeout ? 1 : 0)) {
+        if (threadIdx.x == 0) {
+          atomicExch(a.err, 3);
+          // let the copy already issued for the next tile land before exiting
+          if (e + 1 < re) (void)mbar_wait(&full[(tile + 1) & 1], static_cast<uint32_t>(((tile + 1) >> 1) & 1));
+        }
+        __syncthreads();
+        return;
+      }
+      if (threadIdx.x == 0 && e + 2 < re) issue(e + 2, tile + 2);
+    }
+    tile_base += re - rb;
+#pragma unroll
+    for (int t = 0; t < kTT; ++t) {
+      if (ti[t] < ld) {
+        float* op = a.out + g * a.out_gstride + ti[t];
+#pragma unroll
+        for (int r = 0; r < RC; ++r)
+          if (r < a.Rc) op[r * ld] = acc[t][r];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Scaled source blocks [g][D+1][ld] from float64 coordinates [g][d][ld].
+__global__ void k_scaled_blocks(const double* src, int64_t groups, int d, int D, int ld, int kernel,
+                                double sigma, float* dst) {
+  const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= groups * ld) return;
+  const int64_t g = t / ld;
+  const int i = static_cast<int>(t % ld);
+  double scale;
+  if (kernel == DWFMM_K_GAUSS) scale = sqrt(1.4426950408889634 / (2.0 * sigma * sigma));
+  else if (kernel == DWFMM_K_EXP) scale = 1.4426950408889634 / sigma;
+  else scale = 1.7320508075688772 / sigma;
+  double n2 = 0.0;
+  for (int k = 0; k < D; ++k) {
+    const double v = k < d ? src[(g * d + k) * ld + i] * scale : 0.0;
+    const float f = static_cast<float>(v);
+    dst[(g * (D + 1) + k) * ld + i] = f;
+    n2 += static_cast<double>(f) * static_cast<double>(f);
+  }
+  dst[(g * (D + 1) + D) * ld + i] = static_cast<float>(n2);
+}
+
+template <int D, int RC>
+void launch_kernel_type(int kernel, SumArgs a, int groups, int threads, size_t smem, cudaStream_t s) {
+  switch (kernel) {
+    case DWFMM_K_EXP:
+      k_sum_f32<D, RC, DWFMM_K_EXP><<<groups, threads, smem, s>>>(a);
+      break;
+    case DWFMM_K_MATERN32:
+      k_sum_f32<D, RC, DWFMM_K_MATERN32><<<groups, threads, smem, s>>>(a);
+      break;
+    default:
+      k_sum_f32<D, RC, DWFMM_K_GAUSS><<<groups, threads, smem, s>>>(a);
+  }
+}
+
+template <int D>
+void launch_rc(int kernel, int RC, SumArgs a, int groups, int threads, size_t smem, cudaStream_t s) {
+  if (RC <= 1) launch_kernel_type<D, 1>(kernel, a, groups, threads, smem, s);
+  else if (RC <= 4) launch_kernel_type<D, 4>(kernel, a, groups, threads, smem, s);
+  else if (RC <= 8) launch_kernel_type<D, 8>(kernel, a, groups, threads, smem, s);
+  else launch_kernel_type<D, 16>(kernel, a, groups, threads, smem, s);
+}
+
+template <int D>
+void set_attrs() {
+  const int big = 200 * 1024;
+#define DW_ATTR(RC)                                                                                           \
+  cudaFuncSetAttribute(k_sum_f32<D, RC, DWFMM_K_EXP>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);      \
+  cudaFuncSetAttribute(k_sum_f32<D, RC, DWFMM_K_MATERN32>, cudaFuncAttributeMaxDynamicSharedMemorySize, big); \
+  cudaFuncSetAttribute(k_sum_f32<D, RC, DWFMM_K_GAUSS>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  DW_ATTR(1)
+  DW_ATTR(4)
+  DW_ATTR(8)
+  DW_ATTR(16)
+#undef DW_ATTR
+}
+
+int padded_dim(int d) {
+  if (d <= 4) return 4;
+  if (d <= 8) return 8;
+  if (d <= 10) return 10;
+  if (d <= 12) return 12;
+  if (d <= 16) return 16;
+  return -1;
+}
+
+int padded_rc(int Rc) { return Rc <= 1 ? 1 : Rc <= 4 ? 4 : Rc <= 8 ? 8 : 16; }
+
+void dispatch(int D, int kernel, int RC, SumArgs a, int groups, int threads, size_t smem, cudaStream_t s) {
+  switch (D) {
+    case 4: launch_rc<4>(kernel, RC, a, groups, threads, smem, s); break;
+    case 8: launch_rc<8>(kernel, RC, a, groups, threads, smem, s); break;
+    case 10: launch_rc<10>(kernel, RC, a, groups, threads, smem, s); break;
+    case 12: launch_rc<12>(kernel, RC, a, groups, threads, smem, s); break;
+    default: launch_rc<16>(kernel, RC, a, groups, threads, smem, s); break;
+  }
+}
+
+bool g_attrs_done = false;
+
+void ensure_attrs() {
+  if (g_attrs_done) return;
+  set_attrs<4>();
+  set_attrs<8>();
+  set_attrs<10>();
+  set_attrs<12>();
+  set_attrs<16>();
+  DW_CUDA(cudaGetLastError());
+  g_attrs_done = true;
+}
+
+// Scaled blocks for the current tree: leaf sites and cluster nodes.
+void ensure_scaled(Plan& P, int D) {
+  if (P.dpad == D && P.d_ptsk.p && P.d_ynodek.p) return;
+  const int64_t nl = static_cast<int64_t>(P.L) * (D + 1) * P.m_pad;
+  const int64_t nc = static_cast<int64_t>(P.C) * (D + 1) * P.n_pad;
+  P.d_ptsk.alloc(nl);
+  P.d_ynodek.alloc(nc);
+  k_scaled_blocks<<<ceil_div(static_cast<int64_t>(P.L) * P.m_pad, 256), 256, 0, P.stream>>>(
+      P.d_pts64.p, P.L, P.d, D, P.m_pad, P.kernel, P.sigma, P.d_ptsk.p);
+  k_scaled_blocks<<<ceil_div(static_cast<int64_t>(P.C) * P.n_pad, 256), 256, 0, P.stream>>>(
+      P.d_ynode64.p, P.C, P.d, D, P.n_pad, P.kernel, P.sigma, P.d_ynodek.p);
+  DW_CUDA(cudaGetLastError());
+  P.dpad = D;
+}
+
+size_t stage_bytes(int D, int RC, int ld) { return 2 * static_cast<size_t>((D + 1) * ld + RC * ld) * sizeof(float); }
+
+}  // namespace
+
+bool p2p_f32_tuned(Plan& P, int Rc, cudaStream_t s) {
+  const int D = padded_dim(P.d);
+  if (D < 0) return false;
+  const int RC = padded_rc(Rc);
+  const size_t smem = stage_bytes(D, RC, P.m_pad);
+  if (smem > 200 * 1024) return false;
+  ensure_attrs();
+  ensure_scaled(P, D);
+  // the tree build made the scaled blocks on P.stream; the side stream waits
+  if (s != P.stream) {
+    DW_CUDA(cudaEventRecord(P.ev_scaled, P.stream));
+    DW_CUDA(cudaStreamWaitEvent(s, P.ev_scaled, 0));
+  }
+  SumArgs a{};
+  a.tgt = P.d_ptsk.p;
+  a.tgt_gstride = static_cast<int64_t>(D + 1) * P.m_pad;
+  a.src = P.d_ptsk.p;
+  a.src_gstride = a.tgt_gstride;
+  a.q = P.xb32.p;
+  a.q_gstride = static_cast<int64_t>(kRC) * P.m_pad;
+  a.out = P.ynear32.p;
+  a.out_gstride = a.q_gstride;
+  a.rowptr = P.d_near_rowptr.p;
+  a.col = P.d_near_col.p;
+  a.count = P.d_count.p;
+  a.count_off = P.L - 1;
+  a.count_const = 0;
+  a.first = 0;
+  a.ld = P.m_pad;
+  a.Rc = Rc;
+  a.err = P.d_err.p;
+  const int threads = std::min(kThreadsMax, round_up(ceil_div(P.m_pad, kTT), 32));
+  dispatch(D, P.kernel, RC, a, P.L, threads, smem, s);
+  DW_CUDA(cudaGetLastError());
+  return true;
+}
+
+bool m2l_f32_tuned(Plan& P, int Rc) {
+  const int D = padded_dim(P.d);
+  if (D < 0) return false;
+  const int RC = padded_rc(Rc);
+  const size_t smem = stage_bytes(D, RC, P.n_pad);
+  if (smem > 200 * 1024) return false;
+  ensure_attrs();
+  ensure_scaled(P, D);
+  const int first = (1 << P.jmin) - 1;
+  SumArgs a{};
+  a.tgt = P.d_ynodek.p;
+  a.tgt_gstride = static_cast<int64_t>(D + 1) * P.n_pad;
+  a.src = P.d_ynodek.p;
+  a.src_gstride = a.tgt_gstride;
+  a.q = P.mom32.p;
+  a.q_gstride = static_cast<int64_t>(kRC) * P.n_pad;
+  a.out = P.loc32.p;
+  a.out_gstride = a.q_gstride;
+  a.rowptr = P.d_far_rowptr.p;
+  a.col = P.d_far_col.p;
+  a.count = nullptr;
+  a.count_off = 0;
+  a.count_const = P.n;
+  a.first = first;
+  a.ld = P.n_pad;
+  a.Rc = Rc;
+  a.err = P.d_err.p;
+  const int threads = std::min(kThreadsMax, round_up(ceil_div(P.n_pad, kTT), 32));
+  dispatch(D, P.kernel, RC, a, P.C - first, threads, smem, P.stream);
+  DW_CUDA(cudaGetLastError());
+  return true;
 }
 
 }  // namespace dw

@@ -219,8 +219,8 @@ class Plan:
         self.check(self._l.dwfmm_lists_export(self.h, far.ctypes.data, near.ctypes.data))
         return far, near
 
-    def set_profiling(self, on: bool):
-        self.check(self._l.dwfmm_set_profiling(self.h, 1 if on else 0))
+    def set_profiling(self, on: bool, serialize: bool = False):
+        self.check(self._l.dwfmm_set_profiling(self.h, (2 if serialize else 1) if on else 0))
 
     def phase_times(self, reset: bool = True):
         ms = np.zeros(7)

@@ -414,8 +414,9 @@ def test_planted_transposed_transfer_is_caught(monkeypatch):
     f = np.random.default_rng(2).standard_normal((1, 400))
     pb = o.make_problem(X, "gauss", [1.0, 1.5, 2.0, 3.0], 5.0, 20, 1.0)
     Kt = o.assemble_ktilde(pb)
-    good = o.transfer_matrix
-    monkeypatch.setattr(o, "transfer_matrix", lambda e, t, c: good(e, t, c).T)
+    good = o.problem_transfer
+    pb.cache.clear()
+    monkeypatch.setattr(o, "problem_transfer", lambda p_, c: good(p_, c).T)
     assert o.rel_err(o.fmm_matvec(pb, f), (Kt @ f.T).T) > 1e-6
 
 
@@ -446,3 +447,15 @@ def test_planted_dropped_far_level_is_caught():
     for (t, s) in ls.near:
         cover[tr.begin[t]:tr.end[t], tr.begin[s]:tr.end[s]] += 1
     assert not np.all(cover == 1)
+
+
+def test_vectorised_admissibility_equals_scalar_rule():
+    X = _small(1500, seed=3)
+    tr = o.build_tree(X, 20)
+    rng = np.random.default_rng(0)
+    t = rng.integers(0, tr.nclusters, 4000)
+    s = rng.integers(0, tr.nclusters, 4000)
+    for eta in (0.5, 1.0, 2.0):
+        vec = o.admissible_pairs(tr.lo, tr.hi, t, s, eta)
+        ref = [o.admissible(tr.lo[a], tr.hi[a], tr.lo[b], tr.hi[b], eta) for a, b in zip(t, s)]
+        assert vec.tolist() == ref
