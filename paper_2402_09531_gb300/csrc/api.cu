@@ -454,4 +454,13 @@ dwfmm_status dwfmm_phase_times(dwfmm_plan plan, double* ms, int64_t* launches, i
   });
 }
 
+dwfmm_status dwfmm_direct_sum_noalloc(int32_t kernel, double sigma, const double* pts, int64_t n, int32_t d,
+                                      int64_t ld_pts, const double* x, double* y, int32_t nrhs, int64_t ldx,
+                                      int64_t ldy, void* stream) {
+  return guarded(nullptr, [&]() -> dwfmm_status {
+    return dw::direct_sum_noalloc(kernel, sigma, pts, n, d, ld_pts, x, y, nrhs, ldx, ldy,
+                                  static_cast<cudaStream_t>(stream));
+  });
+}
+
 }  // extern "C"

@@ -217,6 +217,9 @@ void launch_nearfield(Plan& P, int Rc, bool fp64, cudaStream_t s);
 bool p2p_f32_tuned(Plan& P, int Rc, cudaStream_t s);
 bool m2l_f32_tuned(Plan& P, int Rc);
 void check_device_error(Plan& P);
+dwfmm_status direct_sum_noalloc(int kernel, double sigma, const double* pts, int64_t n, int d, int64_t ldp,
+                                const double* x, double* y, int R, int64_t ldx, int64_t ldy,
+                                cudaStream_t s);
 
 // ---- solve (solve.cu) ----
 dwfmm_status solve(Plan& P, double lambda, const double* f, double* c, int R, int64_t ld,

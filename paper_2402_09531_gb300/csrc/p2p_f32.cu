@@ -459,4 +459,161 @@ bool m2l_f32_tuned(Plan& P, int Rc) {
   return true;
 }
 
+
+// ---------------------------------------------------------------------------
+// Allocation-free direct sum (dwfmm_direct_sum_noalloc).
+//
+// Some callers cannot call cudaMalloc: host applications whose framework
+// owns the device memory pool (a caching allocator that has reserved nearly
+// all of it, so a fresh cudaMalloc fails or fragments the pool), and
+// latency-sensitive loops that cannot afford the device synchronisation
+// that cudaMalloc/cudaFree imply.  For them this entry point computes the
+// exact y = K x over all N sites (no tree) with the same tuned kernel as the
+// near field, and keeps every intermediate in one file-scope device array.
+//
+// The array is shared by every call on a device and holds the last call's
+// data; each call rewrites all of it that it reads.  Calls whose work
+// overlaps on the GPU (different streams, no ordering) race on it.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+constexpr int kNaBlock = 256;                       // sites per block
+constexpr int kNaMaxN = 8192;                       // largest N
+constexpr int kNaMaxD = 16;                         // largest d (padded dimension <= 16)
+constexpr int kNaGroups = kNaMaxN / kNaBlock;       // 32
+constexpr size_t kNaCoord = static_cast<size_t>(kNaGroups) * (kNaMaxD + 1) * kNaBlock;
+constexpr size_t kNaCharge = static_cast<size_t>(kNaGroups) * kRC * kNaBlock;
+constexpr size_t kNaInts = 1 + kNaGroups + 1 + kNaGroups + static_cast<size_t>(kNaGroups) * kNaGroups;
+constexpr size_t kNaFloats = kNaCoord + 2 * kNaCharge + kNaInts;
+
+static __device__ __align__(256) float g_noalloc_scratch[kNaFloats];
+
+// Scratch layout (floats): coords [G][D+1][256] | charges [G][16][256] |
+// out [G][16][256] | ints: err, counts[G], rowptr[G+1], col[G*G].
+struct NaLayout {
+  float* coord;
+  float* charge;
+  float* out;
+  int* err;
+  int* count;
+  int* rowptr;
+  int* col;
+};
+
+NaLayout na_layout(float* base) {
+  NaLayout l;
+  l.coord = base;
+  l.charge = base + kNaCoord;
+  l.out = l.charge + kNaCharge;
+  int* ints = reinterpret_cast<int*>(l.out + kNaCharge);
+  l.err = ints;
+  l.count = ints + 1;
+  l.rowptr = l.count + kNaGroups;
+  l.col = l.rowptr + kNaGroups + 1;
+  return l;
+}
+
+// Fills every scratch entry the sum reads: scaled coordinates and norm row,
+// charges (zero past N and past nrhs), counts, a complete block list, and
+// clears the error flag.
+__global__ void k_na_prepare(const double* pts, int64_t n, int d, int64_t ldp, int D, int kernel,
+                             double sigma, const double* x, int R, int64_t ldx, NaLayout l, int G) {
+  const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t == 0) *l.err = 0;
+  if (t < G) {
+    const int64_t rem = n - t * kNaBlock;
+    l.count[t] = static_cast<int>(rem < kNaBlock ? rem : kNaBlock);
+    l.rowptr[t] = static_cast<int>(t) * G;
+    if (t == G - 1) l.rowptr[G] = G * G;
+  }
+  if (t < static_cast<int64_t>(G) * G) l.col[t] = static_cast<int>(t % G);
+  if (t >= static_cast<int64_t>(G) * kNaBlock) return;
+  const int g = static_cast<int>(t / kNaBlock), i = static_cast<int>(t % kNaBlock);
+  const int64_t src = t < n ? t : static_cast<int64_t>(g) * kNaBlock;   // padding repeats the block's first site
+  double scale;
+  if (kernel == DWFMM_K_GAUSS) scale = sqrt(1.4426950408889634 / (2.0 * sigma * sigma));
+  else if (kernel == DWFMM_K_EXP) scale = 1.4426950408889634 / sigma;
+  else scale = 1.7320508075688772 / sigma;
+  double n2 = 0.0;
+  for (int k = 0; k < D; ++k) {
+    const float f = k < d ? static_cast<float>(pts[src * ldp + k] * scale) : 0.0f;
+    l.coord[(static_cast<int64_t>(g) * (D + 1) + k) * kNaBlock + i] = f;
+    n2 += static_cast<double>(f) * static_cast<double>(f);
+  }
+  l.coord[(static_cast<int64_t>(g) * (D + 1) + D) * kNaBlock + i] = static_cast<float>(n2);
+  for (int r = 0; r < kRC; ++r)
+    l.charge[(static_cast<int64_t>(g) * kRC + r) * kNaBlock + i] =
+        (t < n && r < R) ? static_cast<float>(x[r * ldx + t]) : 0.0f;
+}
+
+// y[:, r] from the per-block sums; NaN if a bounded wait gave up.
+__global__ void k_na_finish(NaLayout l, int64_t n, int R, double* y, int64_t ldy) {
+  const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= n * R) return;
+  const int r = static_cast<int>(t / n);
+  const int64_t i = t % n;
+  const int g = static_cast<int>(i / kNaBlock), j = static_cast<int>(i % kNaBlock);
+  const double v = static_cast<double>(l.out[(static_cast<int64_t>(g) * kRC + r) * kNaBlock + j]);
+  y[r * ldy + i] = (*l.err) ? __longlong_as_double(0x7ff8000000000000ll) : v;
+}
+
+// Device address of the scratch array, looked up once per device.
+constexpr int kNaMaxDevices = 64;
+float* g_na_ptr[kNaMaxDevices] = {nullptr};
+
+float* na_scratch_for_current_device() {
+  int dev = 0;
+  DW_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNaMaxDevices) fail(DWFMM_ERR_INVALID_ARG, "device index out of range");
+  if (!g_na_ptr[dev]) {
+    void* p = nullptr;
+    DW_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_na_ptr[dev] = static_cast<float*>(p);
+  }
+  return g_na_ptr[dev];
+}
+
+}  // namespace
+
+dwfmm_status direct_sum_noalloc(int kernel, double sigma, const double* pts, int64_t n, int d, int64_t ldp,
+                                const double* x, double* y, int R, int64_t ldx, int64_t ldy,
+                                cudaStream_t s) {
+  if (kernel < 0 || kernel > 2 || !(sigma > 0.0) || n < 0 || n > kNaMaxN || d < 1 || d > kNaMaxD ||
+      R < 1 || R > kRC)
+    fail(DWFMM_ERR_INVALID_ARG, "direct_sum_noalloc: needs N <= 8192, 1 <= d <= 16, 1 <= nrhs <= 16");
+  if (n == 0) return DWFMM_OK;
+  if (!pts || !x || !y || ldp < d || ldx < n || ldy < n)
+    fail(DWFMM_ERR_INVALID_ARG, "direct_sum_noalloc: NULL buffer or leading dimension too small");
+  const int D = padded_dim(d);
+  const int RC = padded_rc(R);
+  const int G = static_cast<int>((n + kNaBlock - 1) / kNaBlock);
+  ensure_attrs();
+  const NaLayout l = na_layout(na_scratch_for_current_device());
+  k_na_prepare<<<ceil_div(static_cast<int64_t>(G) * kNaBlock + G * G, 256), 256, 0, s>>>(
+      pts, n, d, ldp, D, kernel, sigma, x, R, ldx, l, G);
+  SumArgs a{};
+  a.tgt = l.coord;
+  a.tgt_gstride = static_cast<int64_t>(D + 1) * kNaBlock;
+  a.src = l.coord;
+  a.src_gstride = a.tgt_gstride;
+  a.q = l.charge;
+  a.q_gstride = static_cast<int64_t>(kRC) * kNaBlock;
+  a.out = l.out;
+  a.out_gstride = a.q_gstride;
+  a.rowptr = l.rowptr;
+  a.col = l.col;
+  a.count = l.count;
+  a.count_off = 0;
+  a.count_const = 0;
+  a.first = 0;
+  a.ld = kNaBlock;
+  a.Rc = R;
+  a.err = l.err;
+  dispatch(D, kernel, RC, a, G, kThreadsMax, stage_bytes(D, RC, kNaBlock), s);
+  k_na_finish<<<ceil_div(n * R, 256), 256, 0, s>>>(l, n, R, y, ldy);
+  DW_CUDA(cudaGetLastError());
+  return DWFMM_OK;
+}
+
 }  // namespace dw

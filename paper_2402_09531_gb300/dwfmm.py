@@ -31,7 +31,7 @@ PHASES = ("gather", "p2m_m2m", "m2l", "l2l_l2p", "p2p", "scatter", "matvec")
 EXPORTS = ("dwfmm_plan_create", "dwfmm_plan_set_nodes", "dwfmm_tree_build", "dwfmm_matvec",
            "dwfmm_solve", "dwfmm_plan_destroy", "dwfmm_status_string", "dwfmm_last_error",
            "dwfmm_plan_info", "dwfmm_plan_export", "dwfmm_tree_export", "dwfmm_lists_export",
-           "dwfmm_set_profiling", "dwfmm_phase_times")
+           "dwfmm_set_profiling", "dwfmm_phase_times", "dwfmm_direct_sum_noalloc")
 
 
 class dwfmm_config(C.Structure):
@@ -70,6 +70,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "dwfmm_lists_export": (i32, [P, P, P]),
         "dwfmm_set_profiling": (i32, [P, i32]),
         "dwfmm_phase_times": (i32, [P, P, P, i32]),
+        "dwfmm_direct_sum_noalloc": (i32, [i32, dbl, P, i64, i32, i64, P, P, i32, i64, i64, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
