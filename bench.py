@@ -292,6 +292,9 @@ def run_ours(args):
     clock_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     peak = SMS * FP32_LANES * 2 * clock_mhz * 1e6 / 1e12
     launches = sum(v[1] for k, v in phases.items() if k != "matvec")
+    # DRAM bytes per P2P launch from one ncu capture of this kernel version at this
+    # workload (profiles/p2p_k_sum_f32_gauss_d10.md); None for any other workload.
+    traffic = 14.84e9 if (args.workload == "mixed" and not args.n and args.precision != "fp64") else None
 
     cpu = None
     if cpu_proc is not None:
@@ -319,7 +322,7 @@ def run_ours(args):
                     "d2h_bytes_per_step": int(yh.numel() * 8)},
             "gpu_launches": int(launches),
             "roofline": {"kernel": "p2p (near field)", "bound": "alu", "achieved": achieved, "peak": peak,
-                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                          "flops_per_pair": flops_pair, "pairs_per_launch": pairs,
                          "launch_ms": p2p_avg_ms,
                          "peak_basis": f"{SMS} SMs x {FP32_LANES} FP32 lanes x 2 flop x {clock_mhz:.0f} MHz"},

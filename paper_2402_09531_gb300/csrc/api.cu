@@ -62,6 +62,8 @@ void Plan::free_tree() {
   scratch.release();
   d_ptsk.release();
   d_ynodek.release();
+  xq32.release();
+  momq32.release();
   dpad = -1;
 }
 
@@ -97,6 +99,11 @@ void Plan::free_all() {
   if (ev_join) cudaEventDestroy(ev_join);
   if (ev_scaled) cudaEventDestroy(ev_scaled);
   ev_scaled = nullptr;
+  cgs.d_int.release();
+  if (cgs.h_snap) cudaFreeHost(cgs.h_snap);
+  cgs.h_snap = nullptr;
+  if (cgs.ev) cudaEventDestroy(cgs.ev);
+  cgs.ev = nullptr;
   if (side) cudaStreamDestroy(side);
   ev_fork = ev_join = nullptr;
   side = nullptr;
@@ -450,6 +457,57 @@ dwfmm_status dwfmm_phase_times(dwfmm_plan plan, double* ms, int64_t* launches, i
         P.tm.ms[i] = 0.0;
         P.tm.launches[i] = 0;
       }
+    return DWFMM_OK;
+  });
+}
+
+dwfmm_status dwfmm_cg_begin(dwfmm_plan plan, double lambda, const double* f, int32_t nrhs, int64_t ld,
+                            double rtol, void* stream) {
+  if (!plan) return DWFMM_ERR_INVALID_ARG;
+  Plan& P = plan->P;
+  return guarded(&P, [&]() -> dwfmm_status {
+    if (!P.have_tree) dw::fail(DWFMM_ERR_STATE, "cg_begin before tree_build");
+    if (nrhs < 1 || nrhs > P.max_rhs || nrhs > 64) dw::fail(DWFMM_ERR_INVALID_ARG, "nrhs outside 1..max_rhs");
+    if (!(lambda >= 0.0) || !(rtol > 0.0)) dw::fail(DWFMM_ERR_INVALID_ARG, "lambda or rtol");
+    if (P.N == 0) dw::fail(DWFMM_ERR_INVALID_ARG, "empty problem");
+    if (!f || ld < P.N || !is_device_pointer(f)) dw::fail(DWFMM_ERR_INVALID_ARG, "f must be a device buffer, ld >= N");
+    bind_stream(P, stream);
+    dw::cg_begin(P, lambda, f, nrhs, ld, rtol);
+    return DWFMM_OK;
+  });
+}
+
+dwfmm_status dwfmm_cg_step(dwfmm_plan plan, int32_t iters, void* stream) {
+  if (!plan) return DWFMM_ERR_INVALID_ARG;
+  Plan& P = plan->P;
+  return guarded(&P, [&]() -> dwfmm_status {
+    if (!P.cgs.active) dw::fail(DWFMM_ERR_STATE, "cg_step before cg_begin");
+    if (iters < 0) dw::fail(DWFMM_ERR_INVALID_ARG, "iters < 0");
+    bind_stream(P, stream);
+    dw::cg_step(P, iters);
+    return DWFMM_OK;
+  });
+}
+
+dwfmm_status dwfmm_cg_poll(dwfmm_plan plan, int32_t* ready, int32_t* status, int32_t* iters, double* rr) {
+  if (!plan || !ready) return DWFMM_ERR_INVALID_ARG;
+  Plan& P = plan->P;
+  return guarded(&P, [&]() -> dwfmm_status {
+    if (!P.cgs.active) dw::fail(DWFMM_ERR_STATE, "cg_poll before cg_begin");
+    *ready = dw::cg_poll(P, status, iters, rr) ? 1 : 0;
+    return DWFMM_OK;
+  });
+}
+
+dwfmm_status dwfmm_cg_result(dwfmm_plan plan, double* c, int64_t ld, void* stream) {
+  if (!plan) return DWFMM_ERR_INVALID_ARG;
+  Plan& P = plan->P;
+  return guarded(&P, [&]() -> dwfmm_status {
+    if (!P.cgs.active) dw::fail(DWFMM_ERR_STATE, "cg_result before cg_begin");
+    if (!c || ld < P.N) dw::fail(DWFMM_ERR_INVALID_ARG, "NULL buffer or ld < N");
+    bind_stream(P, stream);
+    dw::cg_result(P, c, ld);
+    if (!is_device_pointer(c)) DW_CUDA(cudaStreamSynchronize(P.stream));
     return DWFMM_OK;
   });
 }

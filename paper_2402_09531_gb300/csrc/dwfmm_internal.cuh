@@ -124,6 +124,16 @@ struct Timers {
   int64_t launches[8] = {0};
 };
 
+// Incremental CG state (device scalars; pinned status snapshot for polling).
+struct CgState {
+  int R = 0;
+  double lam = 0.0, rtol = 1e-6;
+  bool active = false, stepped = false;
+  DBuf<int> d_int;              // status[R], iters[R]
+  int* h_snap = nullptr;        // pinned: status[R], iters[R] | rr[R] at byte 128*4
+  cudaEvent_t ev = nullptr;
+};
+
 struct Plan {
   // configuration
   int d = 0, kernel = 0, wrule = 0, leaf = 0, M = 0, prec = 0, max_rhs = 0;
@@ -181,10 +191,12 @@ struct Plan {
   // tuned float32 kernel summation: scaled blocks [g][dpad+1][ld]
   int dpad = -1;
   DBuf<float> d_ptsk, d_ynodek;
+  DBuf<float> xq32, momq32;   // charges interleaved per source, [g][ld][RC]
   cudaEvent_t ev_scaled = nullptr;
   DBuf<int> d_err;   // device error flag (3 = a bounded wait timed out)
 
   Timers tm;
+  CgState cgs;
 
   ExpDev exp_dev() const {
     return ExpDev{n, n_pad, d, lsum, nnz_max, d_fac.p, d_qk.p, d_loff.p};
@@ -224,6 +236,10 @@ dwfmm_status direct_sum_noalloc(int kernel, double sigma, const double* pts, int
 // ---- solve (solve.cu) ----
 dwfmm_status solve(Plan& P, double lambda, const double* f, double* c, int R, int64_t ld,
                    double rtol, int maxit, int* iters, double* relres);
+void cg_begin(Plan& P, double lam, const double* f, int R, int64_t ld, double rtol);
+void cg_step(Plan& P, int iters);
+bool cg_poll(Plan& P, int* status, int* iters, double* rr);
+void cg_result(Plan& P, double* c, int64_t ld);
 
 inline int ceil_div(int64_t a, int64_t b) { return static_cast<int>((a + b - 1) / b); }
 inline int round_up(int v, int m) { return (v + m - 1) / m * m; }

@@ -15,8 +15,11 @@
 //      exp:       x' = x log2 e / sigma,               phi = ex2(-|x' - s'|)
 //      Matern:    x' = x sqrt3 / sigma,                phi = (1 + r') ex2(-r' log2 e)
 //    so the Gaussian costs D FMAs, one add and one MUFU.EX2 per pair.
+//  - Arithmetic is packed: fma/add/sub.f32x2 (two lanes per instruction) for
+//    distances and accumulation; charges are interleaved per source.
 //  - Per source block the contributions are summed in float32 partials, then
-//    folded into per-target running sums with Kahan compensation.
+//    folded into per-target running sums with Kahan compensation (kept in
+//    shared memory).
 #include <cstdint>
 
 #include "dwfmm_internal.cuh"
@@ -107,13 +110,46 @@ __device__ __forceinline__ float phi_scaled(float a) {
   return fmaf(r, e, e);
 }
 
+// Packed float32 pairs (fma/add/sub .f32x2): one instruction, two lanes of work.
+typedef unsigned long long u64;
+
+__device__ __forceinline__ u64 pk2(float a, float b) {
+  u64 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void up2(u64 v, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ u64 ffma2(u64 a, u64 b, u64 c) {
+  u64 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ u64 fadd2(u64 a, u64 b) {
+  u64 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ u64 fsub2(u64 a, u64 b) {
+  u64 d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
+// Charge blocks are interleaved per source, [g][ld][RC], so RHS pairs are
+// adjacent: (acc_r, acc_r+1) += (phi, phi) * (q_r, q_r+1) is one fma.f32x2.
+// Distances pair up consecutive sources: (e_j, e_j+1) += (2x_k, 2x_k) * (s_jk, s_j+1,k).
 template <int D, int RC, int KER>
 __global__ void __launch_bounds__(kThreadsMax, 3) k_sum_f32(SumArgs a) {
+  constexpr int RP = RC >= 2 ? RC / 2 : 1;   // packed accumulators per target
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[2];
   const int ld = a.ld;
   const int stage_floats = (D + 1) * ld + RC * ld;
   float* stage0 = reinterpret_cast<float*>(smem);
+  // Kahan compensation, [kTT * RP][blockDim] packed pairs (or floats when RC == 1)
+  u64* comp = reinterpret_cast<u64*>(stage0 + 2 * stage_floats);
   const int g = a.first + blockIdx.x;
   const int rb = a.rowptr[g], re = a.rowptr[g + 1];
   const uint32_t coord_bytes = static_cast<uint32_t>((D + 1) * ld * sizeof(float));
@@ -140,9 +176,8 @@ __global__ void __launch_bounds__(kThreadsMax, 3) k_sum_f32(SumArgs a) {
   };
 
   for (int tb = 0; tb < ld; tb += kTT * blockDim.x) {
-    // targets of this thread
-    float xt[kTT][D];
-    float nt[kTT];
+    u64 xt2[kTT][D];   // (c x_k, c x_k), c = 2 for the Gaussian, else 1
+    u64 mnt2[kTT];     // (-|x|^2, -|x|^2) for the Gaussian
     int ti[kTT];
 #pragma unroll
     for (int t = 0; t < kTT; ++t) {
@@ -151,19 +186,23 @@ __global__ void __launch_bounds__(kThreadsMax, 3) k_sum_f32(SumArgs a) {
       const float* tp = a.tgt + g * a.tgt_gstride + i;
 #pragma unroll
       for (int k = 0; k < D; ++k) {
-        const float v = tp[k * ld];
-        xt[t][k] = (KER == DWFMM_K_GAUSS) ? 2.0f * v : v;
+        const float v = (KER == DWFMM_K_GAUSS) ? 2.0f * tp[k * ld] : tp[k * ld];
+        xt2[t][k] = pk2(v, v);
       }
-      nt[t] = (KER == DWFMM_K_GAUSS) ? tp[D * ld] : 0.0f;
+      const float nt = (KER == DWFMM_K_GAUSS) ? -tp[D * ld] : 0.0f;
+      mnt2[t] = pk2(nt, nt);
     }
-    float acc[kTT][RC], comp[kTT][RC];
+    u64 acc[kTT][RP];
+    float acc1[kTT];
 #pragma unroll
-    for (int t = 0; t < kTT; ++t)
+    for (int t = 0; t < kTT; ++t) {
+      acc1[t] = 0.0f;
 #pragma unroll
-      for (int r = 0; r < RC; ++r) {
-        acc[t][r] = 0.0f;
-        comp[t][r] = 0.0f;
+      for (int p = 0; p < RP; ++p) {
+        acc[t][p] = 0ull;
+        comp[(t * RP + p) * blockDim.x + threadIdx.x] = 0ull;
       }
+    }
 
     if (threadIdx.x == 0) {
       if (rb < re) issue(rb, tile_base);
@@ -179,80 +218,105 @@ __global__ void __launch_bounds__(kThreadsMax, 3) k_sum_f32(SumArgs a) {
       const float* sq = sc + (D + 1) * ld;
       const int scnt = a.count ? a.count[a.count_off + a.col[e]] : a.count_const;
       const int s4 = timeout ? 0 : ((scnt + 3) & ~3);
-      float part[kTT][RC];
+      u64 part[kTT][RP];
+      float part1[kTT];
 #pragma unroll
-      for (int t = 0; t < kTT; ++t)
+      for (int t = 0; t < kTT; ++t) {
+        part1[t] = 0.0f;
 #pragma unroll
-        for (int r = 0; r < RC; ++r) part[t][r] = 0.0f;
+        for (int p = 0; p < RP; ++p) part[t][p] = 0ull;
+      }
       for (int j = 0; j < s4; j += 4) {
-        float ph[kTT][4];
+        u64 ph01[kTT], ph23[kTT];
         if (KER == DWFMM_K_GAUSS) {
-          const float4 ns = *reinterpret_cast<const float4*>(sc + D * ld + j);
+          const ulonglong2 ns = *reinterpret_cast<const ulonglong2*>(sc + D * ld + j);
 #pragma unroll
           for (int t = 0; t < kTT; ++t) {
-            ph[t][0] = -(nt[t] + ns.x);
-            ph[t][1] = -(nt[t] + ns.y);
-            ph[t][2] = -(nt[t] + ns.z);
-            ph[t][3] = -(nt[t] + ns.w);
+            ph01[t] = fsub2(mnt2[t], ns.x);
+            ph23[t] = fsub2(mnt2[t], ns.y);
           }
 #pragma unroll
           for (int k = 0; k < D; ++k) {
-            const float4 s = *reinterpret_cast<const float4*>(sc + k * ld + j);
+            const ulonglong2 sv = *reinterpret_cast<const ulonglong2*>(sc + k * ld + j);
 #pragma unroll
             for (int t = 0; t < kTT; ++t) {
-              ph[t][0] = fmaf(xt[t][k], s.x, ph[t][0]);
-              ph[t][1] = fmaf(xt[t][k], s.y, ph[t][1]);
-              ph[t][2] = fmaf(xt[t][k], s.z, ph[t][2]);
-              ph[t][3] = fmaf(xt[t][k], s.w, ph[t][3]);
+              ph01[t] = ffma2(xt2[t][k], sv.x, ph01[t]);
+              ph23[t] = ffma2(xt2[t][k], sv.y, ph23[t]);
             }
           }
         } else {
 #pragma unroll
-          for (int t = 0; t < kTT; ++t) ph[t][0] = ph[t][1] = ph[t][2] = ph[t][3] = 0.0f;
+          for (int t = 0; t < kTT; ++t) ph01[t] = ph23[t] = 0ull;
 #pragma unroll
           for (int k = 0; k < D; ++k) {
-            const float4 s = *reinterpret_cast<const float4*>(sc + k * ld + j);
+            const ulonglong2 sv = *reinterpret_cast<const ulonglong2*>(sc + k * ld + j);
 #pragma unroll
             for (int t = 0; t < kTT; ++t) {
-              float df = xt[t][k] - s.x;
-              ph[t][0] = fmaf(df, df, ph[t][0]);
-              df = xt[t][k] - s.y;
-              ph[t][1] = fmaf(df, df, ph[t][1]);
-              df = xt[t][k] - s.z;
-              ph[t][2] = fmaf(df, df, ph[t][2]);
-              df = xt[t][k] - s.w;
-              ph[t][3] = fmaf(df, df, ph[t][3]);
+              u64 df = fsub2(xt2[t][k], sv.x);
+              ph01[t] = ffma2(df, df, ph01[t]);
+              df = fsub2(xt2[t][k], sv.y);
+              ph23[t] = ffma2(df, df, ph23[t]);
             }
           }
         }
+        float ph[kTT][4];
 #pragma unroll
-        for (int t = 0; t < kTT; ++t)
+        for (int t = 0; t < kTT; ++t) {
+          up2(ph01[t], ph[t][0], ph[t][1]);
+          up2(ph23[t], ph[t][2], ph[t][3]);
 #pragma unroll
           for (int u = 0; u < 4; ++u) ph[t][u] = phi_scaled<KER>(ph[t][u]);
-#pragma unroll
-        for (int r = 0; r < RC; ++r) {
-          const float4 qv = *reinterpret_cast<const float4*>(sq + r * ld + j);
+        }
+        if constexpr (RC == 1) {
+          const float4 qv = *reinterpret_cast<const float4*>(sq + j);
 #pragma unroll
           for (int t = 0; t < kTT; ++t) {
-            float p = part[t][r];
+            float p = part1[t];
             p = fmaf(ph[t][0], qv.x, p);
             p = fmaf(ph[t][1], qv.y, p);
             p = fmaf(ph[t][2], qv.z, p);
             p = fmaf(ph[t][3], qv.w, p);
-            part[t][r] = p;
+            part1[t] = p;
+          }
+        } else {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const ulonglong2* qrow = reinterpret_cast<const ulonglong2*>(sq + (j + u) * RC);
+            u64 f2[kTT];
+#pragma unroll
+            for (int t = 0; t < kTT; ++t) f2[t] = pk2(ph[t][u], ph[t][u]);
+#pragma unroll
+            for (int rr = 0; rr < RC / 4; ++rr) {
+              const ulonglong2 qv = qrow[rr];
+#pragma unroll
+              for (int t = 0; t < kTT; ++t) {
+                part[t][2 * rr] = ffma2(f2[t], qv.x, part[t][2 * rr]);
+                part[t][2 * rr + 1] = ffma2(f2[t], qv.y, part[t][2 * rr + 1]);
+              }
+            }
           }
         }
       }
-      // Kahan: acc += part
+      // Kahan: acc += part (compensation kept in shared memory)
 #pragma unroll
-      for (int t = 0; t < kTT; ++t)
+      for (int t = 0; t < kTT; ++t) {
+        if constexpr (RC == 1) {
+          float* c1 = reinterpret_cast<float*>(comp) + t * blockDim.x + threadIdx.x;
+          const float y = part1[t] - *c1;
+          const float s = acc1[t] + y;
+          *c1 = (s - acc1[t]) - y;
+          acc1[t] = s;
+        } else {
 #pragma unroll
-        for (int r = 0; r < RC; ++r) {
-          const float y = part[t][r] - comp[t][r];
-          const float s = acc[t][r] + y;
-          comp[t][r] = (s - acc[t][r]) - y;
-          acc[t][r] = s;
+          for (int p = 0; p < RP; ++p) {
+            u64* cp = comp + (t * RP + p) * blockDim.x + threadIdx.x;
+            const u64 y = fsub2(part[t][p], *cp);
+            const u64 s = fadd2(acc[t][p], y);
+            *cp = fsub2(fsub2(s, acc[t][p]), y);
+            acc[t][p] = s;
+          }
         }
+      }
       // every thread is done with this stage before it is refilled
       if (__syncthreads_or(timeout ? 1 : 0)) {
         if (threadIdx.x == 0) {
@@ -270,13 +334,32 @@ __global__ void __launch_bounds__(kThreadsMax, 3) k_sum_f32(SumArgs a) {
     for (int t = 0; t < kTT; ++t) {
       if (ti[t] < ld) {
         float* op = a.out + g * a.out_gstride + ti[t];
+        if constexpr (RC == 1) {
+          if (a.Rc > 0) op[0] = acc1[t];
+        } else {
 #pragma unroll
-        for (int r = 0; r < RC; ++r)
-          if (r < a.Rc) op[r * ld] = acc[t][r];
+          for (int p = 0; p < RP; ++p) {
+            float lo, hi;
+            up2(acc[t][p], lo, hi);
+            if (2 * p < a.Rc) op[(2 * p) * ld] = lo;
+            if (2 * p + 1 < a.Rc) op[(2 * p + 1) * ld] = hi;
+          }
+        }
       }
     }
     __syncthreads();
   }
+}
+
+// Row layout [g][16][ld] -> interleaved [g][ld][RC] (first RC rows).
+__global__ void k_interleave(const float* src, int64_t groups, int ld, int RC, float* dst) {
+  const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= groups * ld * RC) return;
+  const int r = static_cast<int>(t % RC);
+  const int64_t gi = t / RC;
+  const int i = static_cast<int>(gi % ld);
+  const int64_t g = gi / ld;
+  dst[t] = src[(g * kRC + r) * ld + i];
 }
 
 // Scaled source blocks [g][D+1][ld] from float64 coordinates [g][d][ld].
@@ -385,7 +468,10 @@ void ensure_scaled(Plan& P, int D) {
   P.dpad = D;
 }
 
-size_t stage_bytes(int D, int RC, int ld) { return 2 * static_cast<size_t>((D + 1) * ld + RC * ld) * sizeof(float); }
+size_t stage_bytes(int D, int RC, int ld) {
+  const size_t comp = static_cast<size_t>(kTT) * (RC >= 2 ? RC / 2 : 1) * kThreadsMax * sizeof(unsigned long long);
+  return 2 * static_cast<size_t>((D + 1) * ld + RC * ld) * sizeof(float) + comp;
+}
 
 }  // namespace
 
@@ -402,15 +488,18 @@ bool p2p_f32_tuned(Plan& P, int Rc, cudaStream_t s) {
     DW_CUDA(cudaEventRecord(P.ev_scaled, P.stream));
     DW_CUDA(cudaStreamWaitEvent(s, P.ev_scaled, 0));
   }
+  P.xq32.alloc(static_cast<size_t>(P.L) * P.m_pad * kRC);
+  const int64_t nq = static_cast<int64_t>(P.L) * P.m_pad * RC;
+  k_interleave<<<ceil_div(nq, 256), 256, 0, s>>>(P.xb32.p, P.L, P.m_pad, RC, P.xq32.p);
   SumArgs a{};
   a.tgt = P.d_ptsk.p;
   a.tgt_gstride = static_cast<int64_t>(D + 1) * P.m_pad;
   a.src = P.d_ptsk.p;
   a.src_gstride = a.tgt_gstride;
-  a.q = P.xb32.p;
-  a.q_gstride = static_cast<int64_t>(kRC) * P.m_pad;
+  a.q = P.xq32.p;
+  a.q_gstride = static_cast<int64_t>(RC) * P.m_pad;
   a.out = P.ynear32.p;
-  a.out_gstride = a.q_gstride;
+  a.out_gstride = static_cast<int64_t>(kRC) * P.m_pad;
   a.rowptr = P.d_near_rowptr.p;
   a.col = P.d_near_col.p;
   a.count = P.d_count.p;
@@ -435,15 +524,18 @@ bool m2l_f32_tuned(Plan& P, int Rc) {
   ensure_attrs();
   ensure_scaled(P, D);
   const int first = (1 << P.jmin) - 1;
+  P.momq32.alloc(static_cast<size_t>(P.C) * P.n_pad * kRC);
+  const int64_t nq = static_cast<int64_t>(P.C) * P.n_pad * RC;
+  k_interleave<<<ceil_div(nq, 256), 256, 0, P.stream>>>(P.mom32.p, P.C, P.n_pad, RC, P.momq32.p);
   SumArgs a{};
   a.tgt = P.d_ynodek.p;
   a.tgt_gstride = static_cast<int64_t>(D + 1) * P.n_pad;
   a.src = P.d_ynodek.p;
   a.src_gstride = a.tgt_gstride;
-  a.q = P.mom32.p;
-  a.q_gstride = static_cast<int64_t>(kRC) * P.n_pad;
+  a.q = P.momq32.p;
+  a.q_gstride = static_cast<int64_t>(RC) * P.n_pad;
   a.out = P.loc32.p;
-  a.out_gstride = a.q_gstride;
+  a.out_gstride = static_cast<int64_t>(kRC) * P.n_pad;
   a.rowptr = P.d_far_rowptr.p;
   a.col = P.d_far_col.p;
   a.count = nullptr;
@@ -518,7 +610,7 @@ NaLayout na_layout(float* base) {
 // charges (zero past N and past nrhs), counts, a complete block list, and
 // clears the error flag.
 __global__ void k_na_prepare(const double* pts, int64_t n, int d, int64_t ldp, int D, int kernel,
-                             double sigma, const double* x, int R, int64_t ldx, NaLayout l, int G) {
+                             double sigma, const double* x, int R, int RC, int64_t ldx, NaLayout l, int G) {
   const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t == 0) *l.err = 0;
   if (t < G) {
@@ -542,8 +634,8 @@ __global__ void k_na_prepare(const double* pts, int64_t n, int d, int64_t ldp, i
     n2 += static_cast<double>(f) * static_cast<double>(f);
   }
   l.coord[(static_cast<int64_t>(g) * (D + 1) + D) * kNaBlock + i] = static_cast<float>(n2);
-  for (int r = 0; r < kRC; ++r)
-    l.charge[(static_cast<int64_t>(g) * kRC + r) * kNaBlock + i] =
+  for (int r = 0; r < RC; ++r)   // interleaved per site: [g][256][RC]
+    l.charge[(static_cast<int64_t>(g) * kNaBlock + i) * RC + r] =
         (t < n && r < R) ? static_cast<float>(x[r * ldx + t]) : 0.0f;
 }
 
@@ -591,16 +683,16 @@ dwfmm_status direct_sum_noalloc(int kernel, double sigma, const double* pts, int
   ensure_attrs();
   const NaLayout l = na_layout(na_scratch_for_current_device());
   k_na_prepare<<<ceil_div(static_cast<int64_t>(G) * kNaBlock + G * G, 256), 256, 0, s>>>(
-      pts, n, d, ldp, D, kernel, sigma, x, R, ldx, l, G);
+      pts, n, d, ldp, D, kernel, sigma, x, R, RC, ldx, l, G);
   SumArgs a{};
   a.tgt = l.coord;
   a.tgt_gstride = static_cast<int64_t>(D + 1) * kNaBlock;
   a.src = l.coord;
   a.src_gstride = a.tgt_gstride;
   a.q = l.charge;
-  a.q_gstride = static_cast<int64_t>(kRC) * kNaBlock;
+  a.q_gstride = static_cast<int64_t>(RC) * kNaBlock;
   a.out = l.out;
-  a.out_gstride = a.q_gstride;
+  a.out_gstride = static_cast<int64_t>(kRC) * kNaBlock;
   a.rowptr = l.rowptr;
   a.col = l.col;
   a.count = l.count;

@@ -231,3 +231,151 @@ dwfmm_status solve(Plan& P, double lam, const double* f, double* c, int R, int64
 }
 
 }  // namespace dw
+
+// ---------------------------------------------------------------------------
+// Incremental CG with every scalar on the device (for many solves in flight).
+// One iteration is a fixed sequence of launches on the plan's stream with no
+// host synchronisation: Ap = K_tilde p + lambda p, pAp, alpha, x/r update,
+// rr_new, beta (convergence and breakdown decided per column on the device),
+// p update.  A non-blocking poll reads a status snapshot copied to pinned
+// host memory after each batch of iterations.
+// ---------------------------------------------------------------------------
+
+namespace dw {
+
+namespace {
+
+// state layout (doubles): rr[R], pap[R], coef[R], bn2[R]; ints: status[R], iters[R]
+__global__ void k_cg_init(const double* rr, int R, double* st_rr, double* st_bn2, int* status, int* iters,
+                          double rtol) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= R) return;
+  st_rr[r] = rr[r];
+  st_bn2[r] = rr[r];
+  iters[r] = 0;
+  status[r] = (rr[r] == 0.0) ? 1 : 0;   // 0 running, 1 converged, 2 breakdown
+  (void)rtol;
+}
+
+__global__ void k_cg_alpha(const double* pap, const double* rr, int* status, double* alpha, int R) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= R) return;
+  double a = 0.0;
+  if (status[r] == 0) {
+    if (!(pap[r] > 0.0)) status[r] = 2;
+    else a = rr[r] / pap[r];
+  }
+  alpha[r] = a;
+}
+
+__global__ void k_cg_beta(const double* rr_new, double* rr, const double* bn2, int* status, int* iters,
+                          double* beta, int R, double rtol2) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= R) return;
+  double b = 0.0;
+  if (status[r] == 0) {
+    iters[r] += 1;
+    if (rr_new[r] <= rtol2 * bn2[r]) status[r] = 1;
+    b = rr_new[r] / rr[r];
+    rr[r] = rr_new[r];
+  }
+  beta[r] = b;
+}
+
+void dots_dev(Plan& P, const double* a, const double* b, int64_t n, int R, double* part, double* out) {
+  dim3 grid(kDotBlocks, R);
+  k_dot_partial<<<grid, kDotThreads, 0, P.stream>>>(a, b, n, n, part);
+  k_dot_final<<<ceil_div(R, 64), 64, 0, P.stream>>>(part, kDotBlocks, R, out);
+}
+
+}  // namespace
+
+void cg_begin(Plan& P, double lam, const double* f, int R, int64_t ld, double rtol) {
+  const int64_t n = P.N;
+  const int64_t nr = n * R;
+  CgState& S = P.cgs;
+  S.R = R;
+  S.lam = lam;
+  S.rtol = rtol;
+  S.active = true;
+  P.cg_r.alloc(nr);
+  P.cg_p.alloc(nr);
+  P.cg_ap.alloc(nr);
+  P.cg_c.alloc(nr);
+  P.cg_f.alloc(nr);
+  P.cg_dot.alloc(static_cast<size_t>(kDotBlocks) * R + 8 * R + 8);
+  S.d_int.alloc(2 * R);
+  if (!S.h_snap) DW_CUDA(cudaMallocHost(reinterpret_cast<void**>(&S.h_snap), 64 * (2 * sizeof(int) + sizeof(double))));
+  if (!S.ev) DW_CUDA(cudaEventCreateWithFlags(&S.ev, cudaEventDisableTiming));
+  double* part = P.cg_dot.p;
+  double* rr = part + kDotBlocks * R;
+  double* pap = rr + R;
+  double* coef = pap + R;
+  double* bn2 = coef + R;
+  double* tmp = bn2 + R;
+  DW_CUDA(cudaMemcpy2DAsync(P.cg_f.p, n * sizeof(double), f, ld * sizeof(double), n * sizeof(double), R,
+                            cudaMemcpyDeviceToDevice, P.stream));
+  DW_CUDA(cudaMemsetAsync(P.cg_c.p, 0, nr * sizeof(double), P.stream));
+  DW_CUDA(cudaMemcpyAsync(P.cg_r.p, P.cg_f.p, nr * sizeof(double), cudaMemcpyDeviceToDevice, P.stream));
+  DW_CUDA(cudaMemcpyAsync(P.cg_p.p, P.cg_f.p, nr * sizeof(double), cudaMemcpyDeviceToDevice, P.stream));
+  dots_dev(P, P.cg_r.p, P.cg_r.p, n, R, part, tmp);
+  k_cg_init<<<1, 64, 0, P.stream>>>(tmp, R, rr, bn2, S.d_int.p, S.d_int.p + R, rtol);
+  DW_CUDA(cudaGetLastError());
+}
+
+void cg_step(Plan& P, int iters) {
+  CgState& S = P.cgs;
+  const int64_t n = P.N;
+  const int R = S.R;
+  const int64_t nr = n * R;
+  double* part = P.cg_dot.p;
+  double* rr = part + kDotBlocks * R;
+  double* pap = rr + R;
+  double* coef = pap + R;
+  double* bn2 = coef + R;
+  double* tmp = bn2 + R;
+  int* status = S.d_int.p;
+  int* its = S.d_int.p + R;
+  const bool fp64 = P.prec == DWFMM_P_FP64;
+  for (int k = 0; k < iters; ++k) {
+    apply_op(P, P.cg_p.p, P.cg_ap.p, R, S.lam, fp64);
+    dots_dev(P, P.cg_p.p, P.cg_ap.p, n, R, part, pap);
+    k_cg_alpha<<<1, 64, 0, P.stream>>>(pap, rr, status, coef, R);
+    k_axpby<<<ceil_div(nr, 256), 256, 0, P.stream>>>(P.cg_p.p, P.cg_c.p, nullptr, coef, 1.0, nullptr, 0.0, n, n, R, 1.0);
+    k_axpby<<<ceil_div(nr, 256), 256, 0, P.stream>>>(P.cg_ap.p, P.cg_r.p, nullptr, coef, 1.0, nullptr, 0.0, n, n, R, -1.0);
+    dots_dev(P, P.cg_r.p, P.cg_r.p, n, R, part, tmp);
+    k_cg_beta<<<1, 64, 0, P.stream>>>(tmp, rr, bn2, status, its, coef, R, S.rtol * S.rtol);
+    k_axpby<<<ceil_div(nr, 256), 256, 0, P.stream>>>(P.cg_r.p, P.cg_p.p, nullptr, nullptr, 0.0, coef, 0.0, n, n, R, 1.0);
+  }
+  // status snapshot for the non-blocking poll
+  DW_CUDA(cudaMemcpyAsync(S.h_snap, S.d_int.p, 2 * R * sizeof(int), cudaMemcpyDeviceToHost, P.stream));
+  DW_CUDA(cudaMemcpyAsync(reinterpret_cast<char*>(S.h_snap) + 128 * sizeof(int), rr, R * sizeof(double),
+                          cudaMemcpyDeviceToHost, P.stream));
+  DW_CUDA(cudaEventRecord(S.ev, P.stream));
+  S.stepped = true;
+  DW_CUDA(cudaGetLastError());
+}
+
+// Returns true when the snapshot of the last cg_step is available.
+bool cg_poll(Plan& P, int* status, int* iters, double* rr) {
+  CgState& S = P.cgs;
+  if (!S.stepped) return false;
+  const cudaError_t e = cudaEventQuery(S.ev);
+  if (e == cudaErrorNotReady) return false;
+  DW_CUDA(e);
+  const int R = S.R;
+  for (int r = 0; r < R; ++r) {
+    if (status) status[r] = S.h_snap[r];
+    if (iters) iters[r] = S.h_snap[R + r];
+    if (rr) rr[r] = reinterpret_cast<const double*>(reinterpret_cast<const char*>(S.h_snap) + 128 * sizeof(int))[r];
+  }
+  return true;
+}
+
+void cg_result(Plan& P, double* c, int64_t ld) {
+  const int64_t n = P.N;
+  DW_CUDA(cudaMemcpy2DAsync(c, ld * sizeof(double), P.cg_c.p, n * sizeof(double), n * sizeof(double), P.cgs.R,
+                            cudaMemcpyDefault, P.stream));
+}
+
+}  // namespace dw
