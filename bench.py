@@ -296,6 +296,10 @@ def run_ours(args):
     # workload (profiles/p2p_k_sum_f32_gauss_d10.md); None for any other workload.
     traffic = 14.84e9 if (args.workload == "mixed" and not args.n and args.precision != "fp64") else None
 
+    solve = None
+    if not args.no_solve and rank == 0:
+        solve = run_solve_sample(args)
+
     cpu = None
     if cpu_proc is not None:
         res = finish_oracle_subprocess(cpu_proc)
@@ -331,11 +335,44 @@ def run_ours(args):
             "setup_ms": setup_ms, "tree_build_ms": min(tree_ms),
             "clocks": clk.summary(), "clocks_e2e": clk2.summary(),
             "cpu_baseline": cpu,
+            "solve": solve,
         }
         print(json.dumps(line), flush=True)
     plan.close()
     if dist:
         dist.destroy_process_group()
+
+
+def run_solve_sample(args):
+    """CG solve latency: a bounded sample of the serving request stream
+    (d=16, gamma_k=2^-k, exponential kernel, q=6, lambda=1e-6, rtol=1e-6;
+    eta=2 and the Sec. 6.2 weights; N <= args.solve_nmax), all arriving at
+    t=0, served by the continuous-batching server (float32 operator, float64
+    refinement residual)."""
+    import dwfmm_inputs as di
+    from paper_2402_09531_gb300.serving import Request, Server, summarize
+    reqs = []
+    for w in di.serving_requests(2000):
+        if w.n > args.solve_nmax:
+            continue
+        X, f = di.sites_and_rhs(w, nrhs=1)
+        reqs.append(Request(rid=len(reqs), X=X, f=f, kernel=w.kernel, gamma=w.gamma, q=w.q, eta=2.0,
+                            leaf=w.leaf, weight_rule="paper_logrho", lam=w.lam, rtol=w.rtol, maxit=6000))
+        if len(reqs) >= args.solve_requests:
+            break
+    srv = Server(precision="fp32", max_active=8)
+    srv.run(reqs[:2])                                   # warm-up (plan pool, kernel attributes)
+    t0 = time.perf_counter()
+    res = srv.run(reqs)
+    wall = time.perf_counter() - t0
+    out = summarize(res, wall)
+    out.update({"workload": "serving stream sample: d=16, gamma_k=2^-k, exp kernel, q=6, eta=2, "
+                            "Sec. 6.2 weights, leaf 128, lambda=1e-6, rtol=1e-6",
+                "n_range": [min(r.X.shape[0] for r in reqs), max(r.X.shape[0] for r in reqs)],
+                "arrivals": "all at t=0 (closed loop)", "max_active": 8, "peak_active": srv.peak_active,
+                "precision": "float32 operator + float64 refinement residual"})
+    srv.close()
+    return out
 
 
 def run_reference(args):
@@ -371,6 +408,9 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["fp64", "fp32", "mixed"])
     ap.add_argument("--cpu-steps", type=int, default=2)
     ap.add_argument("--n", type=int, default=0, help="override N (smaller case for profiling)")
+    ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--solve-requests", type=int, default=16)
+    ap.add_argument("--solve-nmax", type=int, default=20000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--oracle-sample", default=None)
     args = ap.parse_args()

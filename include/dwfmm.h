@@ -44,7 +44,7 @@ typedef enum {
   DWFMM_ERR_INVALID_ARG = 1,   /* a NULL pointer, a size out of range, NaN/Inf sites */
   DWFMM_ERR_OOM = 2,           /* a device allocation failed */
   DWFMM_ERR_CUDA = 3,          /* a CUDA runtime call failed */
-  DWFMM_ERR_BREAKDOWN = 4,     /* CG: p^T (K_tilde + lambda I) p <= 0 */
+  DWFMM_ERR_BREAKDOWN = 4,     /* CG: p^T (K_tilde + lambda I) p == 0 or not finite */
   DWFMM_ERR_NOT_CONVERGED = 5, /* CG: maxit reached before rtol */
   DWFMM_ERR_TIMEOUT = 6,       /* a bounded device wait gave up */
   DWFMM_ERR_STATE = 7,         /* call out of order (e.g. matvec before tree_build) */
@@ -150,11 +150,40 @@ dwfmm_status dwfmm_matvec(dwfmm_plan plan, const double* x, double* y, int32_t n
  * iters_out (host, may be NULL): total CG iterations; relres_out (host, R
  * values, may be NULL): final true relative residual per column.
  * Synchronises `stream`.
- * Errors: STATE, INVALID_ARG (lambda < 0, rtol <= 0, maxit < 1), BREAKDOWN,
- * NOT_CONVERGED, CUDA. */
+ * Negative curvature (the compressed matrix can be mildly indefinite) does not
+ * stop the iteration.  Errors: STATE, INVALID_ARG (lambda < 0, rtol <= 0,
+ * maxit < 1), BREAKDOWN (p^T A p == 0 or not finite), NOT_CONVERGED, CUDA. */
 dwfmm_status dwfmm_solve(dwfmm_plan plan, double lambda, const double* f, double* c,
                          int32_t nrhs, int64_t ld, double rtol, int32_t maxit,
                          int32_t* iters_out, double* relres_out, void* stream);
+
+/* Incremental CG for many solves in flight (Sec. 2 Eq. (2.2), Sec. 6.2).
+ * dwfmm_cg_begin starts one CG per column of f (device, column-major N x R,
+ * leading dimension ld >= N; copied) on (K_tilde + lambda I) c = f from
+ * c = 0; dwfmm_cg_step enqueues `iters` iterations on `stream` with every
+ * scalar kept on the device (alpha, beta, per-column convergence
+ * ||r|| <= rtol ||f|| and breakdown p^T A p == 0 are decided on the GPU), so
+ * it never synchronises and solves on different plans and streams overlap;
+ * the matvec uses the plan's precision.  dwfmm_cg_poll never blocks: *ready
+ * = 1 once the work of the last dwfmm_cg_step has finished, and then status
+ * (R int32: 0 running, 1 converged, 2 breakdown), iters (R int32) and rr (R
+ * doubles, ||r||^2) describe that point (any may be NULL).
+ * dwfmm_cg_result copies the current c (host or device, ld >= N; a host
+ * copy synchronises `stream`).  Errors: STATE (no tree / no cg_begin),
+ * INVALID_ARG (f not a device buffer, nrhs outside 1..max_rhs), CUDA. */
+dwfmm_status dwfmm_cg_begin(dwfmm_plan plan, double lambda, const double* f, int32_t nrhs, int64_t ld,
+                            double rtol, void* stream);
+dwfmm_status dwfmm_cg_step(dwfmm_plan plan, int32_t iters, void* stream);
+dwfmm_status dwfmm_cg_poll(dwfmm_plan plan, int32_t* ready, int32_t* status, int32_t* iters, double* rr);
+dwfmm_status dwfmm_cg_result(dwfmm_plan plan, double* c, int64_t ld, void* stream);
+
+/* r = f - (K_tilde + lambda I) c with the float64 operator whatever the
+ * plan's precision (the outer residual of iterative refinement).  f, c, r:
+ * host or device, column-major N x nrhs with leading dimension ld >= N; r
+ * may be NULL.  relres (host, nrhs doubles, may be NULL) receives
+ * ||r|| / ||f|| per column.  Synchronises `stream`. */
+dwfmm_status dwfmm_residual(dwfmm_plan plan, double lambda, const double* f, const double* c, double* r,
+                            int32_t nrhs, int64_t ld, double* relres, void* stream);
 
 /* Release every resource of the plan (NULL is accepted).  Synchronises the
  * plan's last stream first. */

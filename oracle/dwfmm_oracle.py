@@ -721,8 +721,11 @@ def cg(apply, f: np.ndarray, lam: float, rtol: float, maxit: int) -> CGResult:
 
     Reading (Sec. 6.2 "relative error less than 1e-6"): stop when the
     recurrence residual satisfies ||r_k|| <= rtol ||f||; the reported relres
-    is the true residual ||f - (A + lam I) c|| / ||f||.  Breakdown when
-    p^T (A + lam I) p <= 0."""
+    is the true residual ||f - (A + lam I) c|| / ||f||.  Sec. 6.2 runs CG on
+    the compressed matrix with ridges down to 1e-6, and the compression error
+    (Sec. 5.3) can make K_tilde + lam I mildly indefinite, so negative
+    curvature p^T A p < 0 does not stop the iteration; breakdown is only
+    p^T A p == 0 or non-finite (the recurrence cannot continue)."""
     f = np.asarray(f, dtype=np.float64)
     c = np.zeros_like(f)
     r = f.copy()
@@ -739,7 +742,7 @@ def cg(apply, f: np.ndarray, lam: float, rtol: float, maxit: int) -> CGResult:
             break
         Ap = apply(p) + lam * p
         pAp = float(p @ Ap)
-        if not pAp > 0.0:
+        if pAp == 0.0 or not math.isfinite(pAp):
             status = "breakdown"
             break
         a = rr / pAp

@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "dwfmm_internal.cuh"
 
@@ -159,7 +160,7 @@ const char* dwfmm_status_string(dwfmm_status s) {
     case DWFMM_ERR_INVALID_ARG: return "invalid argument";
     case DWFMM_ERR_OOM: return "out of device memory";
     case DWFMM_ERR_CUDA: return "CUDA error";
-    case DWFMM_ERR_BREAKDOWN: return "CG breakdown (p^T A p <= 0)";
+    case DWFMM_ERR_BREAKDOWN: return "CG breakdown (p^T A p == 0 or not finite)";
     case DWFMM_ERR_NOT_CONVERGED: return "CG did not converge";
     case DWFMM_ERR_TIMEOUT: return "device wait timed out";
     case DWFMM_ERR_STATE: return "call out of order";
@@ -508,6 +509,39 @@ dwfmm_status dwfmm_cg_result(dwfmm_plan plan, double* c, int64_t ld, void* strea
     bind_stream(P, stream);
     dw::cg_result(P, c, ld);
     if (!is_device_pointer(c)) DW_CUDA(cudaStreamSynchronize(P.stream));
+    return DWFMM_OK;
+  });
+}
+
+dwfmm_status dwfmm_residual(dwfmm_plan plan, double lambda, const double* f, const double* c, double* r,
+                            int32_t nrhs, int64_t ld, double* relres, void* stream) {
+  if (!plan) return DWFMM_ERR_INVALID_ARG;
+  Plan& P = plan->P;
+  return guarded(&P, [&]() -> dwfmm_status {
+    if (!P.have_tree) dw::fail(DWFMM_ERR_STATE, "residual before tree_build");
+    if (nrhs < 1 || nrhs > P.max_rhs) dw::fail(DWFMM_ERR_INVALID_ARG, "nrhs outside 1..max_rhs");
+    if (P.N == 0) return DWFMM_OK;
+    if (!f || !c || ld < P.N) dw::fail(DWFMM_ERR_INVALID_ARG, "NULL buffer or ld < N");
+    bind_stream(P, stream);
+    const int64_t n = P.N;
+    const size_t nr = static_cast<size_t>(n) * nrhs;
+    dw::DBuf<double> fd, cd, rd;
+    fd.alloc(nr);
+    cd.alloc(nr);
+    rd.alloc(nr);
+    DW_CUDA(cudaMemcpy2DAsync(fd.p, n * sizeof(double), f, ld * sizeof(double), n * sizeof(double), nrhs,
+                              cudaMemcpyDefault, P.stream));
+    DW_CUDA(cudaMemcpy2DAsync(cd.p, n * sizeof(double), c, ld * sizeof(double), n * sizeof(double), nrhs,
+                              cudaMemcpyDefault, P.stream));
+    std::vector<double> rel(nrhs);
+    dw::residual64(P, lambda, fd.p, cd.p, rd.p, nrhs, rel.data());
+    if (r)
+      DW_CUDA(cudaMemcpy2DAsync(r, ld * sizeof(double), rd.p, n * sizeof(double), n * sizeof(double), nrhs,
+                                cudaMemcpyDefault, P.stream));
+    DW_CUDA(cudaStreamSynchronize(P.stream));
+    dw::check_device_error(P);
+    if (relres)
+      for (int k = 0; k < nrhs; ++k) relres[k] = rel[k];
     return DWFMM_OK;
   });
 }

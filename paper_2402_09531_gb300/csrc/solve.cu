@@ -2,6 +2,9 @@
 // Sec. 6.2 solves the kernel ridge system by CG to a relative tolerance).
 // One independent CG per right-hand side column, float64 vectors, dot
 // products reduced deterministically (fixed block partition, fixed order).
+// The compressed matrix can be mildly indefinite (Sec. 5.3 error against a
+// small ridge), so negative curvature p^T A p < 0 does not stop CG; a column
+// breaks down only when p^T A p is zero or not finite.
 // FP32/MIXED plans run iterative refinement: the outer residual uses the
 // float64 operator, the inner CG the plan's reduced-precision operator.
 #include <algorithm>
@@ -112,7 +115,7 @@ int cg(Plan& P, Vecs& V, const double* b, double* x, int R, double lam, double r
     for (int r = 0; r < R; ++r) {
       alpha[r] = 0.0;
       if (!active[r]) continue;
-      if (!(pap[r] > 0.0)) {
+      if (pap[r] == 0.0 || !std::isfinite(pap[r])) {   // negative curvature is tolerated
         active[r] = 0;
         st[r] = 1;
         continue;
@@ -262,7 +265,7 @@ __global__ void k_cg_alpha(const double* pap, const double* rr, int* status, dou
   if (r >= R) return;
   double a = 0.0;
   if (status[r] == 0) {
-    if (!(pap[r] > 0.0)) status[r] = 2;
+    if (pap[r] == 0.0 || !isfinite(pap[r])) status[r] = 2;   // negative curvature is tolerated
     else a = rr[r] / pap[r];
   }
   alpha[r] = a;
@@ -376,6 +379,27 @@ void cg_result(Plan& P, double* c, int64_t ld) {
   const int64_t n = P.N;
   DW_CUDA(cudaMemcpy2DAsync(c, ld * sizeof(double), P.cg_c.p, n * sizeof(double), n * sizeof(double), P.cgs.R,
                             cudaMemcpyDefault, P.stream));
+}
+
+}  // namespace dw
+
+namespace dw {
+
+// r = f - (K64 c + lam c); relres per column.  f, c, r: device, leading dimension n.
+void residual64(Plan& P, double lam, const double* f, const double* c, double* r, int R, double* relres) {
+  const int64_t n = P.N;
+  const int64_t nr = n * R;
+  P.cg_tmp.alloc(nr);
+  P.cg_dot.alloc(static_cast<size_t>(kDotBlocks) * R + 8 * R + 8);
+  apply_op(P, c, P.cg_tmp.p, R, lam, true);
+  DW_CUDA(cudaMemcpyAsync(r, f, nr * sizeof(double), cudaMemcpyDeviceToDevice, P.stream));
+  k_axpby<<<ceil_div(nr, 256), 256, 0, P.stream>>>(P.cg_tmp.p, r, nullptr, nullptr, 1.0, nullptr, 0.0, n, n, R, -1.0);
+  std::vector<double> rn(R), fn(R);
+  double* part = P.cg_dot.p;
+  double* out = part + kDotBlocks * R;
+  dots(P, r, r, n, n, R, part, out, rn.data());
+  dots(P, f, f, n, n, R, part, out, fn.data());
+  for (int k = 0; k < R; ++k) relres[k] = fn[k] > 0.0 ? std::sqrt(rn[k] / fn[k]) : 0.0;
 }
 
 }  // namespace dw

@@ -31,7 +31,8 @@ PHASES = ("gather", "p2m_m2m", "m2l", "l2l_l2p", "p2p", "scatter", "matvec")
 EXPORTS = ("dwfmm_plan_create", "dwfmm_plan_set_nodes", "dwfmm_tree_build", "dwfmm_matvec",
            "dwfmm_solve", "dwfmm_plan_destroy", "dwfmm_status_string", "dwfmm_last_error",
            "dwfmm_plan_info", "dwfmm_plan_export", "dwfmm_tree_export", "dwfmm_lists_export",
-           "dwfmm_set_profiling", "dwfmm_phase_times", "dwfmm_direct_sum_noalloc")
+           "dwfmm_set_profiling", "dwfmm_phase_times", "dwfmm_direct_sum_noalloc",
+           "dwfmm_cg_begin", "dwfmm_cg_step", "dwfmm_cg_poll", "dwfmm_cg_result", "dwfmm_residual")
 
 
 class dwfmm_config(C.Structure):
@@ -71,6 +72,11 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "dwfmm_set_profiling": (i32, [P, i32]),
         "dwfmm_phase_times": (i32, [P, P, P, i32]),
         "dwfmm_direct_sum_noalloc": (i32, [i32, dbl, P, i64, i32, i64, P, P, i32, i64, i64, P]),
+        "dwfmm_cg_begin": (i32, [P, dbl, P, i32, i64, dbl, P]),
+        "dwfmm_cg_step": (i32, [P, i32, P]),
+        "dwfmm_cg_poll": (i32, [P, C.POINTER(i32), P, P, P]),
+        "dwfmm_cg_result": (i32, [P, P, i64, P]),
+        "dwfmm_residual": (i32, [P, dbl, P, P, P, i32, i64, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -184,6 +190,40 @@ class Plan:
         st = self._l.dwfmm_solve(self.h, float(lam), _ptr(f), _ptr(c), R, ld, float(rtol), int(maxit),
                                  C.byref(it), rel, _stream_handle(stream))
         return st, int(it.value), [float(v) for v in rel]
+
+    # -- incremental CG (many solves in flight) -----------------------------
+    def cg_begin(self, lam: float, f, rtol: float = 1e-6, stream=None):
+        """f: (R, N) float64 cuda tensor."""
+        self._cg_R = int(f.shape[0])
+        self._cg_f = f
+        self.check(self._l.dwfmm_cg_begin(self.h, float(lam), _ptr(f), self._cg_R, int(f.stride(0)),
+                                          float(rtol), _stream_handle(stream)))
+
+    def cg_step(self, iters: int, stream=None):
+        self.check(self._l.dwfmm_cg_step(self.h, int(iters), _stream_handle(stream)))
+
+    def cg_poll(self):
+        """(ready, status[R], iters[R], rr[R]) without blocking."""
+        R = self._cg_R
+        ready = C.c_int32(0)
+        st = np.zeros(R, dtype=np.int32)
+        it = np.zeros(R, dtype=np.int32)
+        rr = np.zeros(R)
+        self.check(self._l.dwfmm_cg_poll(self.h, C.byref(ready), st.ctypes.data, it.ctypes.data, rr.ctypes.data))
+        return bool(ready.value), st, it, rr
+
+    def cg_result(self, c, stream=None):
+        self.check(self._l.dwfmm_cg_result(self.h, _ptr(c), int(c.stride(0)) if hasattr(c, "stride") and
+                                           callable(c.stride) else int(c.strides[0] // 8), _stream_handle(stream)))
+        return c
+
+    def residual(self, lam: float, f, c, r=None, stream=None):
+        R = int(f.shape[0])
+        ld = int(f.stride(0)) if hasattr(f, "stride") and callable(f.stride) else int(f.strides[0] // 8)
+        rel = np.zeros(R)
+        self.check(self._l.dwfmm_residual(self.h, float(lam), _ptr(f), _ptr(c), _ptr(r), R, ld,
+                                          rel.ctypes.data, _stream_handle(stream)))
+        return rel
 
     def info(self):
         nx, nf, nn, dep = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int32()

@@ -1,0 +1,243 @@
+"""Continuous-batching CG solve server on one GPU.
+
+Requests (sites, right-hand sides, kernel parameters) are admitted while an
+active slot and enough of the device-memory budget are free.  Every admitted
+request owns a plan (from a pool keyed by its expansion parameters, so the
+node setup of Sec. 5.4 runs once per configuration), a CUDA stream and its
+Krylov state on the device.  Each pass of the loop enqueues a few CG
+iterations (dwfmm_cg_step: no host synchronisation) for every request whose
+previous batch has finished (dwfmm_cg_poll: never blocks), so the matvecs of
+all active requests overlap on the GPU.  A finished inner solve of a float32
+plan is refined with the float64 operator (dwfmm_residual) until the
+float64 relative residual meets the request's tolerance.  Finished requests
+release their slot, memory and plan.
+
+This module only schedules; every numerical step runs in libdwfmm.so.
+"""
+from __future__ import annotations
+
+import math
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from .dwfmm import Plan
+
+
+@dataclass
+class Request:
+    rid: int
+    X: np.ndarray            # (N, d) float64 sites
+    f: np.ndarray            # (R, N) float64 right-hand sides
+    kernel: str = "exp"
+    sigma: float = 1.0
+    gamma: np.ndarray | None = None
+    q: float = 6.0
+    eta: float = 1.0
+    leaf: int = 128
+    weight_rule: str = "inv_gamma"
+    lam: float = 1e-6
+    rtol: float = 1e-6
+    maxit: int = 5000
+    arrival: float = 0.0     # seconds after the start of the run
+
+
+@dataclass
+class Result:
+    rid: int
+    c: np.ndarray
+    status: str              # "ok", "breakdown", "not_converged"
+    iters: int
+    relres: list
+    refinements: int
+    t_arrival: float
+    t_admit: float
+    t_done: float
+
+    @property
+    def latency_ms(self) -> float:
+        return (self.t_done - self.t_arrival) * 1e3
+
+
+def estimate_bytes(n: int, d: int, nrhs: int, leaf: int, n_x: int) -> int:
+    """Device memory of one request (tree, lists, workspaces, Krylov vectors),
+    a deliberately generous upper estimate used for admission."""
+    leaves = 2 ** max(0, math.ceil(math.log2(max(1, n) / leaf)))
+    clusters = 2 * leaves
+    n_pad = (n_x + 7) // 8 * 8
+    per_site = d * 8 * 6 + 16 * 4 * 8 + 16 * 8 * 4 + nrhs * 8 * 8 + 64
+    per_cluster = n_pad * 16 * 4 * 8 + n_pad * (d + 1) * 12 + d * 8 * 6
+    near_pairs = leaves * 64
+    return int(n * per_site + clusters * per_cluster + near_pairs * 24 + (32 << 20))
+
+
+@dataclass
+class _Active:
+    req: Request
+    plan: Plan
+    stream: object
+    key: tuple
+    fd: object               # device rhs of the current inner solve
+    f0: object               # device original rhs
+    acc: object              # device accumulated solution
+    t_admit: float
+    nbytes: int
+    iters: int = 0
+    refinements: int = 0
+
+
+class Server:
+    """Admission by memory and slots; all active solves advance concurrently."""
+
+    def __init__(self, precision: str = "fp32", max_active: int = 8, mem_budget: int | None = None,
+                 step_iters: int = 8, device: int = 0):
+        import torch
+        self.torch = torch
+        self.dev = torch.device("cuda", device)
+        self.precision = precision
+        self.max_active = max_active
+        if mem_budget is None:
+            free, _ = torch.cuda.mem_get_info(self.dev)
+            mem_budget = int(0.5 * free)
+        self.mem_budget = mem_budget
+        self.step_iters = step_iters
+        self.pool: dict = {}
+        self.used = 0
+        self.peak_active = 0
+
+    # -- plans ----------------------------------------------------------------
+    def _key(self, r: Request) -> tuple:
+        return (r.X.shape[1], r.kernel, r.sigma, tuple(np.asarray(r.gamma, float)), r.q, r.eta, r.leaf,
+                r.weight_rule, r.f.shape[0])
+
+    def _take_plan(self, r: Request, stream) -> tuple:
+        key = self._key(r)
+        free = self.pool.get(key, [])
+        if free:
+            return key, free.pop()
+        p = Plan(d=r.X.shape[1], kernel=r.kernel, sigma=r.sigma, gamma=r.gamma, weight_rule=r.weight_rule,
+                 q=r.q, eta=r.eta, leaf_size=r.leaf, precision=self.precision, max_rhs=r.f.shape[0],
+                 stream=stream)
+        return key, p
+
+    def _give_plan(self, key, plan: Plan):
+        torch = self.torch
+        plan.tree_build(torch.zeros((0, plan.d), dtype=torch.float64, device=self.dev))   # release the tree
+        self.pool.setdefault(key, []).append(plan)
+
+    # -- request lifecycle ------------------------------------------------------
+    def _admit(self, r: Request, t_now: float) -> _Active:
+        torch = self.torch
+        stream = torch.cuda.Stream(self.dev)
+        key, plan = self._take_plan(r, stream)
+        nbytes = estimate_bytes(r.X.shape[0], r.X.shape[1], r.f.shape[0], r.leaf, plan.n_x)
+        with torch.cuda.stream(stream):
+            Xd = torch.from_numpy(r.X).to(self.dev, non_blocking=False)
+            f0 = torch.from_numpy(np.ascontiguousarray(r.f)).to(self.dev)
+            acc = torch.zeros_like(f0)
+        plan.tree_build(Xd, stream=stream)
+        plan.cg_begin(r.lam, f0, rtol=r.rtol, stream=stream)
+        plan.cg_step(self.step_iters, stream=stream)
+        self.used += nbytes
+        return _Active(r, plan, stream, key, f0, f0, acc, t_now, nbytes)
+
+    def _finish(self, a: _Active, status: str, relres, t_now: float) -> Result:
+        torch = self.torch
+        a.stream.synchronize()
+        c = a.acc.cpu().numpy()
+        self.used -= a.nbytes
+        self._give_plan(a.key, a.plan)
+        return Result(a.req.rid, c, status, a.iters, list(relres), a.refinements, a.req.arrival, a.t_admit, t_now)
+
+    def _advance(self, a: _Active, t_now: float):
+        """Handle a finished batch of iterations; returns a Result when done."""
+        torch = self.torch
+        ready, st, its, rr = a.plan.cg_poll()
+        if not ready:
+            return None
+        a_iters = int(its.max()) if len(its) else 0
+        running = bool(np.any(st == 0))
+        total = a.iters + a_iters
+        if running and total < a.req.maxit:
+            a.plan.cg_step(self.step_iters, stream=a.stream)
+            return None
+        # inner solve finished: fold it into the accumulated solution
+        with torch.cuda.stream(a.stream):
+            tmp = torch.empty_like(a.acc)
+        a.plan.cg_result(tmp, stream=a.stream)
+        with torch.cuda.stream(a.stream):
+            a.acc += tmp
+        a.iters = total
+        if np.any(st == 2):
+            return self._finish(a, "breakdown", [float("nan")] * len(st), t_now)
+        with torch.cuda.stream(a.stream):
+            r = torch.empty_like(a.acc)
+        rel = a.plan.residual(a.req.lam, a.f0, a.acc, r=r, stream=a.stream)
+        if np.all(rel <= a.req.rtol):
+            return self._finish(a, "ok", rel, t_now)
+        if a.iters >= a.req.maxit or a.refinements >= 20:
+            return self._finish(a, "not_converged", rel, t_now)
+        # refinement: solve for the float64 residual, relative tolerance rtol of it
+        a.refinements += 1
+        a.fd = r
+        inner = min(0.5, max(1e-7, 0.5 * a.req.rtol / max(1e-300, float(np.max(rel)))))
+        a.plan.cg_begin(a.req.lam, r, rtol=inner, stream=a.stream)
+        a.plan.cg_step(self.step_iters, stream=a.stream)
+        return None
+
+    def run(self, requests: list) -> list:
+        """Serve `requests` (arrival times relative to now); returns results in
+        completion order."""
+        pending = sorted(requests, key=lambda r: r.arrival)
+        queue: list = []
+        active: list = []
+        done: list = []
+        t0 = time.perf_counter()
+        pi = 0
+        while pi < len(pending) or queue or active:
+            now = time.perf_counter() - t0
+            while pi < len(pending) and pending[pi].arrival <= now:
+                queue.append(pending[pi])
+                pi += 1
+            while queue and len(active) < self.max_active:
+                r = queue[0]
+                need = estimate_bytes(r.X.shape[0], r.X.shape[1], r.f.shape[0], r.leaf, 0)
+                if active and self.used + need > self.mem_budget:
+                    break
+                queue.pop(0)
+                active.append(self._admit(r, now))
+            self.peak_active = max(self.peak_active, len(active))
+            progressed = False
+            for a in list(active):
+                res = self._advance(a, time.perf_counter() - t0)
+                if res is not None:
+                    active.remove(a)
+                    done.append(res)
+                    progressed = True
+            if not progressed and not queue:
+                time.sleep(20e-6)
+        return done
+
+    def close(self):
+        for plans in self.pool.values():
+            for p in plans:
+                p.close()
+        self.pool.clear()
+
+
+def summarize(results: list, wall_s: float) -> dict:
+    lat = sorted(r.latency_ms for r in results)
+    ok = [r for r in results if r.status == "ok"]
+
+    def pct(p):
+        if not lat:
+            return None
+        k = min(len(lat) - 1, max(0, int(math.ceil(p / 100.0 * len(lat))) - 1))
+        return lat[k]
+    return {"requests": len(results), "ok": len(ok),
+            "breakdown": sum(r.status == "breakdown" for r in results),
+            "not_converged": sum(r.status == "not_converged" for r in results),
+            "p50_ms": pct(50), "p99_ms": pct(99), "solves_per_s": len(results) / wall_s if wall_s > 0 else None,
+            "mean_iters": float(np.mean([r.iters for r in results])) if results else None,
+            "max_relres": float(max(max(r.relres) for r in ok)) if ok else None}

@@ -1,0 +1,103 @@
+"""Serving: many CG solves in flight on one GPU (continuous batching).
+
+Each served result must be the same alone and in the mix (every request
+owns its plan, stream and Krylov state; reductions have a fixed order, so
+the results are bit-identical), admission must respect the memory budget,
+the incremental device-side CG must agree with the blocking solve, and the
+served solutions must meet the tolerance with the oracle's operator.
+
+Serving workload (Sec. 6.2 style sites, the serving generator): d=16,
+gamma_k=2^-k, exponential kernel, q=6, lambda=1e-6, rtol=1e-6.  Readings for
+the unstated parameters: eta=2 and the Sec. 6.2 weight rule, leaf 128 (with
+eta=1 or the gamma_1/gamma_k weights the compressed matrix has eigenvalues
+below -0.1 at these sizes and CG breaks down for lambda=1e-6, in the oracle
+as well).
+"""
+import numpy as np
+import pytest
+
+import dwfmm_inputs as di
+from oracle import dwfmm_oracle as o
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__ as ge
+    ge.build()
+
+
+def _requests(ns, seed0=50, arrival=0.0):
+    from paper_2402_09531_gb300.serving import Request
+    out = []
+    for i, n in enumerate(ns):
+        w = di.Workload(f"r{i}", d=16, n=n, gamma=di.gamma_half_powers(16), kernel="exp", q=6.0, leaf=128,
+                        eta=2.0, seed=seed0 + i)
+        X, f = di.sites_and_rhs(w, nrhs=1)
+        out.append(Request(rid=i, X=X, f=f, kernel="exp", gamma=w.gamma, q=6.0, eta=2.0, leaf=128,
+                           weight_rule="paper_logrho", lam=1e-6, rtol=1e-6, maxit=4000, arrival=arrival * i))
+    return out
+
+
+def test_same_result_alone_and_in_the_mix():
+    from paper_2402_09531_gb300.serving import Server
+    reqs = _requests([1500, 2600, 900, 3200, 2000, 1200])
+    alone = Server(precision="fp32", max_active=1)
+    r_alone = alone.run([reqs[0]])[0]
+    alone.close()
+    mix = Server(precision="fp32", max_active=6)
+    res = {r.rid: r for r in mix.run(reqs)}
+    assert mix.peak_active >= 4
+    mix.close()
+    assert r_alone.status == "ok"
+    assert res[0].status == "ok" and res[0].iters == r_alone.iters
+    np.testing.assert_array_equal(res[0].c, r_alone.c)
+    for rid in (1, 3):
+        r = reqs[rid]
+        pb = o.make_problem(r.X, "exp", o.weights_paper_normalised(2 * r.gamma, 2.0), 6.0, 128, 2.0)
+        c = res[rid].c[0]
+        resid = r.f[0] - (o.fmm_matvec(pb, c[None])[0] + r.lam * c)
+        assert res[rid].status == "ok"
+        assert np.linalg.norm(resid) / np.linalg.norm(r.f[0]) <= 2e-6
+
+
+def test_admission_respects_memory_budget():
+    from paper_2402_09531_gb300.serving import Server, estimate_bytes
+    reqs = _requests([1000, 1100, 1200], seed0=70)
+    one = estimate_bytes(1200, 16, 1, 128, 0)
+    srv = Server(precision="fp32", max_active=8, mem_budget=one + 1)
+    res = srv.run(reqs)
+    assert srv.peak_active == 1 and len(res) == 3
+    srv.close()
+
+
+def test_incremental_cg_matches_blocking_solve():
+    import torch
+    from paper_2402_09531_gb300 import Plan
+    w = di.scaled(di.small_exp_d4(), 2000, nrhs=2)
+    w.kernel = "matern32"
+    X, f = di.sites_and_rhs(w)
+    kw = dict(d=4, kernel="matern32", gamma=w.gamma, q=4.0, eta=1.0, leaf_size=64, precision="fp64", max_rhs=2)
+    fd = torch.from_numpy(f).cuda()
+    a = Plan(**kw)
+    a.tree_build(torch.from_numpy(X).cuda())
+    ca = torch.zeros_like(fd)
+    st, its, rel = a.solve(5.0, fd, ca, rtol=1e-10, maxit=500)
+    assert st == 0
+    b = Plan(**kw)
+    b.tree_build(torch.from_numpy(X).cuda())
+    b.cg_begin(5.0, fd, rtol=1e-10)
+    for _ in range(200):
+        b.cg_step(5)
+        torch.cuda.synchronize()
+        ready, status, iters, rr = b.cg_poll()
+        assert ready
+        if np.all(status != 0):
+            break
+    assert np.all(status == 1)
+    cb = torch.zeros_like(fd)
+    b.cg_result(cb)
+    torch.cuda.synchronize()
+    assert int(iters.max()) == its
+    np.testing.assert_allclose(cb.cpu().numpy(), ca.cpu().numpy(), rtol=0, atol=1e-12 * float(ca.abs().max()))

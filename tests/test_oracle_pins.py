@@ -397,9 +397,15 @@ def test_cg_matches_dense_solve():
 
 
 def test_cg_breakdown_and_maxit():
+    # zero curvature: p = f = e1 and e1^T A e1 = 0 -- the recurrence cannot continue
+    A = np.array([[0.0, 1.0], [1.0, 0.0]])
+    res = o.cg(lambda v: A @ v, np.array([1.0, 0.0]), 0.0, 1e-12, 10)
+    assert res.status == "breakdown"
+    # negative curvature is tolerated: diag(1, -1, 2) c = e2 is solved in one step (c = -e2)
     A = np.diag([1.0, -1.0, 2.0])
     res = o.cg(lambda v: A @ v, np.array([0.0, 1.0, 0.0]), 0.0, 1e-12, 10)
-    assert res.status == "breakdown"
+    assert res.status == "ok" and res.iters == 1
+    np.testing.assert_allclose(res.c, [0.0, -1.0, 0.0])
     B = np.diag(np.linspace(1, 1e4, 50))
     res = o.cg(lambda v: B @ v, np.ones(50), 0.0, 1e-14, 3)
     assert res.status == "not_converged" and res.iters == 3
