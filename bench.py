@@ -343,36 +343,45 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def run_solve_sample(args):
-    """CG solve latency: a bounded sample of the serving request stream
-    (d=16, gamma_k=2^-k, exponential kernel, q=6, lambda=1e-6, rtol=1e-6;
-    eta=2 and the Sec. 6.2 weights; N <= args.solve_nmax), all arriving at
-    t=0, served by the continuous-batching server (float32 operator, float64
-    refinement residual)."""
-    import dwfmm_inputs as di
+def _serve(reqs, precision, lam):
     from paper_2402_09531_gb300.serving import Request, Server, summarize
+    rs = [Request(rid=r.rid, X=r.X, f=r.f, kernel=r.kernel, gamma=r.gamma, q=r.q, eta=r.eta, leaf=r.leaf,
+                  weight_rule=r.weight_rule, lam=lam, rtol=r.rtol, maxit=r.maxit) for r in reqs]
+    srv = Server(precision=precision, max_active=8)
+    srv.run(rs[:1])                                     # warm-up (plan pool, kernel attributes)
+    t0 = time.perf_counter()
+    res = srv.run(rs)
+    out = summarize(res, time.perf_counter() - t0)
+    out.update({"precision": precision, "lambda": lam, "peak_active": srv.peak_active})
+    srv.close()
+    return out
+
+
+def run_solve_sample(args):
+    """CG solve latency on a bounded sample of the serving request stream
+    (d=16, gamma_k=2^-k, exponential kernel, q=6, rtol=1e-6; eta=2 and the
+    Sec. 6.2 weights; N <= args.solve_nmax), all arriving at t=0 and served
+    by the continuous-batching server.  lambda=1e-6 needs the float64
+    operator (the float32 operator's rounding exceeds lambda by orders of
+    magnitude and refinement diverges); float32 + float64-residual
+    refinement is compared with float64 at lambda=1e-2."""
+    import dwfmm_inputs as di
+    from paper_2402_09531_gb300.serving import Request
     reqs = []
     for w in di.serving_requests(2000):
         if w.n > args.solve_nmax:
             continue
         X, f = di.sites_and_rhs(w, nrhs=1)
         reqs.append(Request(rid=len(reqs), X=X, f=f, kernel=w.kernel, gamma=w.gamma, q=w.q, eta=2.0,
-                            leaf=w.leaf, weight_rule="paper_logrho", lam=w.lam, rtol=w.rtol, maxit=6000))
+                            leaf=w.leaf, weight_rule="paper_logrho", lam=w.lam, rtol=w.rtol, maxit=4000))
         if len(reqs) >= args.solve_requests:
             break
-    srv = Server(precision="fp32", max_active=8)
-    srv.run(reqs[:2])                                   # warm-up (plan pool, kernel attributes)
-    t0 = time.perf_counter()
-    res = srv.run(reqs)
-    wall = time.perf_counter() - t0
-    out = summarize(res, wall)
-    out.update({"workload": "serving stream sample: d=16, gamma_k=2^-k, exp kernel, q=6, eta=2, "
-                            "Sec. 6.2 weights, leaf 128, lambda=1e-6, rtol=1e-6",
-                "n_range": [min(r.X.shape[0] for r in reqs), max(r.X.shape[0] for r in reqs)],
-                "arrivals": "all at t=0 (closed loop)", "max_active": 8, "peak_active": srv.peak_active,
-                "precision": "float32 operator + float64 refinement residual"})
-    srv.close()
-    return out
+    return {"workload": "serving stream sample: d=16, gamma_k=2^-k, exp kernel, q=6, eta=2, Sec. 6.2 weights, "
+                        "leaf 128, rtol=1e-6, all arriving at t=0, 8 active slots",
+            "n_range": [min(r.X.shape[0] for r in reqs), max(r.X.shape[0] for r in reqs)],
+            "fp64_lambda_1e-6": _serve(reqs, "fp64", 1e-6),
+            "fp64_lambda_1e-2": _serve(reqs, "fp64", 1e-2),
+            "mixed_lambda_1e-2": _serve(reqs, "mixed", 1e-2)}
 
 
 def run_reference(args):
@@ -409,8 +418,8 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=2)
     ap.add_argument("--n", type=int, default=0, help="override N (smaller case for profiling)")
     ap.add_argument("--no-solve", action="store_true")
-    ap.add_argument("--solve-requests", type=int, default=16)
-    ap.add_argument("--solve-nmax", type=int, default=20000)
+    ap.add_argument("--solve-requests", type=int, default=8)
+    ap.add_argument("--solve-nmax", type=int, default=3000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--oracle-sample", default=None)
     args = ap.parse_args()

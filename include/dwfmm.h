@@ -185,6 +185,43 @@ dwfmm_status dwfmm_cg_result(dwfmm_plan plan, double* c, int64_t ld, void* strea
 dwfmm_status dwfmm_residual(dwfmm_plan plan, double lambda, const double* f, const double* c, double* r,
                             int32_t nrhs, int64_t ld, double* relres, void* stream);
 
+/* The kernel interpolant at new points (Sec. 2: s_X(x) = sum_j alpha_j
+ * K(x_j, x); Sec. 6.2 measures its prediction error at test points):
+ * out(t, r) = sum_j phi(||x_t - x_j|| / sigma) c(j, r) for t < nt, evaluated
+ * exactly (every target against every site, no compression) in the plan's
+ * precision (float32 plans: d <= 20).  targets (host or device): nt x d
+ * row-major, leading dimension ld_t >= d; c (host or device): column-major
+ * N x nrhs, ld_c >= N, the caller's site order; out (host or device):
+ * column-major nt x nrhs, ld_o >= nt.  Synchronises `stream`.
+ * Errors: STATE (no tree), INVALID_ARG, OOM, CUDA, TIMEOUT. */
+dwfmm_status dwfmm_evaluate(dwfmm_plan plan, const double* targets, int64_t nt, int64_t ld_t, const double* c,
+                            int64_t ld_c, double* out, int64_t ld_o, int32_t nrhs, void* stream);
+
+/* Batches: many uneven problems in one fused matvec (float32 plans).
+ * dwfmm_batch_create groups `count` plans whose trees are built, with equal
+ * kernel, index-set size |Lambda| and leaf block size (equal leaf_size and
+ * N >= leaf_size), d <= 16 and precision FP32 or MIXED; nrhs[i] (1..16) is
+ * the number of right-hand sides of problem i for every later call.  The
+ * near field of all problems is one launch of the kernel-summation engine,
+ * the couplings (M2L) of all problems another, the upward and downward
+ * passes one launch per tree height/level; the launch shape of the two fused
+ * launches (one padded launch or one per right-hand-side class) is chosen by
+ * timing both once, and the whole sequence is captured as a CUDA graph.
+ * The plans must stay alive and keep their trees while the batch exists.
+ * Synchronises `stream` before it starts.
+ * dwfmm_batch_matvec: y[i] = K_tilde_i x[i] for every problem, x[i] and y[i]
+ * device buffers, column-major N_i x nrhs[i] with leading dimension N_i;
+ * enqueued on `stream` (one graph launch).
+ * dwfmm_batch_info: split (1 if one launch per class was faster), tune_ms
+ * (2 doubles: padded, per class) and the total number of leaves.
+ * Errors: INVALID_ARG, STATE (a plan without a tree), OOM, CUDA. */
+typedef struct dwfmm_batch_s* dwfmm_batch;
+dwfmm_status dwfmm_batch_create(const dwfmm_plan* plans, const int32_t* nrhs, int32_t count, void* stream,
+                                dwfmm_batch* out);
+dwfmm_status dwfmm_batch_matvec(dwfmm_batch batch, const double* const* x, double* const* y, void* stream);
+dwfmm_status dwfmm_batch_info(dwfmm_batch batch, int32_t* split, double* tune_ms, int64_t* leaves);
+dwfmm_status dwfmm_batch_destroy(dwfmm_batch batch);
+
 /* Release every resource of the plan (NULL is accepted).  Synchronises the
  * plan's last stream first. */
 dwfmm_status dwfmm_plan_destroy(dwfmm_plan plan);

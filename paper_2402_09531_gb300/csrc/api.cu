@@ -12,10 +12,6 @@ using dw::ApiError;
 using dw::CudaError;
 using dw::Plan;
 
-struct dwfmm_plan_s {
-  Plan P;
-};
-
 namespace dw {
 
 void Plan::free_tree() {
@@ -544,6 +540,100 @@ dwfmm_status dwfmm_residual(dwfmm_plan plan, double lambda, const double* f, con
       for (int k = 0; k < nrhs; ++k) relres[k] = rel[k];
     return DWFMM_OK;
   });
+}
+
+dwfmm_status dwfmm_evaluate(dwfmm_plan plan, const double* targets, int64_t nt, int64_t ld_t, const double* c,
+                            int64_t ld_c, double* out, int64_t ld_o, int32_t nrhs, void* stream) {
+  if (!plan) return DWFMM_ERR_INVALID_ARG;
+  Plan& P = plan->P;
+  return guarded(&P, [&]() -> dwfmm_status {
+    if (!P.have_tree) dw::fail(DWFMM_ERR_STATE, "evaluate before tree_build");
+    if (nrhs < 1 || nrhs > P.max_rhs) dw::fail(DWFMM_ERR_INVALID_ARG, "nrhs outside 1..max_rhs");
+    if (nt < 0) dw::fail(DWFMM_ERR_INVALID_ARG, "nt < 0");
+    if (nt == 0 || P.N == 0) return DWFMM_OK;
+    if (!targets || !c || !out || ld_t < P.d || ld_c < P.N || ld_o < nt)
+      dw::fail(DWFMM_ERR_INVALID_ARG, "NULL buffer or leading dimension too small");
+    bind_stream(P, stream);
+    const size_t ntr = static_cast<size_t>(nt) * nrhs;
+    dw::DBuf<double> ts, cs, os;
+    const double* td = targets;
+    const double* cd = c;
+    double* od = out;
+    int64_t lt = ld_t, lc = ld_c, lo = ld_o;
+    if (!is_device_pointer(targets)) {
+      ts.alloc(static_cast<size_t>(nt) * ld_t);
+      DW_CUDA(cudaMemcpyAsync(ts.p, targets, sizeof(double) * nt * ld_t, cudaMemcpyHostToDevice, P.stream));
+      td = ts.p;
+    }
+    if (!is_device_pointer(c)) {
+      cs.alloc(static_cast<size_t>(P.N) * nrhs);
+      DW_CUDA(cudaMemcpy2DAsync(cs.p, P.N * sizeof(double), c, ld_c * sizeof(double), P.N * sizeof(double), nrhs,
+                                cudaMemcpyHostToDevice, P.stream));
+      cd = cs.p;
+      lc = P.N;
+    }
+    const bool oh = !is_device_pointer(out);
+    if (oh) {
+      os.alloc(ntr);
+      od = os.p;
+      lo = nt;
+    }
+    dw::evaluate(P, td, nt, lt, cd, lc, od, lo, nrhs);
+    if (oh)
+      DW_CUDA(cudaMemcpy2DAsync(out, ld_o * sizeof(double), od, nt * sizeof(double), nt * sizeof(double), nrhs,
+                                cudaMemcpyDeviceToHost, P.stream));
+    DW_CUDA(cudaStreamSynchronize(P.stream));
+    dw::check_device_error(P);
+    return DWFMM_OK;
+  });
+}
+
+struct dwfmm_batch_s {
+  dw::Batch* B = nullptr;
+};
+
+dwfmm_status dwfmm_batch_create(const dwfmm_plan* plans, const int32_t* nrhs, int32_t count, void* stream,
+                                dwfmm_batch* out) {
+  if (!plans || !nrhs || !out || count < 1) return DWFMM_ERR_INVALID_ARG;
+  *out = nullptr;
+  std::vector<Plan*> ps(count);
+  for (int i = 0; i < count; ++i) {
+    if (!plans[i]) return DWFMM_ERR_INVALID_ARG;
+    ps[i] = &plans[i]->P;
+  }
+  dw::Batch* b = dw::batch_new();
+  const dwfmm_status st = guarded(ps[0], [&]() -> dwfmm_status {
+    if (stream) DW_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    dw::batch_create(*b, ps.data(), nrhs, count);
+    return DWFMM_OK;
+  });
+  if (st != DWFMM_OK) {
+    dw::batch_delete(b);
+    return st;
+  }
+  *out = new dwfmm_batch_s{b};
+  return DWFMM_OK;
+}
+
+dwfmm_status dwfmm_batch_matvec(dwfmm_batch batch, const double* const* x, double* const* y, void* stream) {
+  if (!batch || !x || !y) return DWFMM_ERR_INVALID_ARG;
+  return guarded(nullptr, [&]() -> dwfmm_status {
+    dw::batch_matvec(*batch->B, x, y, static_cast<cudaStream_t>(stream));
+    return DWFMM_OK;
+  });
+}
+
+dwfmm_status dwfmm_batch_info(dwfmm_batch batch, int32_t* split, double* tune_ms, int64_t* leaves) {
+  if (!batch) return DWFMM_ERR_INVALID_ARG;
+  dw::batch_info(*batch->B, split, tune_ms, leaves);
+  return DWFMM_OK;
+}
+
+dwfmm_status dwfmm_batch_destroy(dwfmm_batch batch) {
+  if (!batch) return DWFMM_OK;
+  dw::batch_delete(batch->B);
+  delete batch;
+  return DWFMM_OK;
 }
 
 dwfmm_status dwfmm_direct_sum_noalloc(int32_t kernel, double sigma, const double* pts, int64_t n, int32_t d,

@@ -1,0 +1,406 @@
+// Many uneven DW-FMM problems in one fused matvec (float32).
+//
+// A batch concatenates the problems' scaled source blocks, charges, outputs
+// and far/near lists into single arrays with global CSR lists, so that the
+// near field (P2P) of every problem is one launch of the kernel-summation
+// engine and the couplings (M2L) of every problem another; the upward and
+// downward passes are one launch per tree height / level over a work list of
+// (problem, cluster) items that reads each problem's arrays from a device
+// table.  The whole sequence is captured once into a CUDA graph and replayed.
+//
+// Autotuning: the problems are ordered by their padded right-hand-side class
+// (1, 4, 8, 16); at creation the P2P+M2L work is timed both as one launch
+// padded to the largest class and as one launch per class, and the faster
+// shape is captured.
+#include <algorithm>
+#include <numeric>
+#include <vector>
+
+#include "dwfmm_internal.cuh"
+
+namespace dw {
+
+struct Batch {
+  std::vector<Plan*> plans;   // internal order
+  std::vector<int> order;     // internal index -> caller index
+  std::vector<int> R;
+  int P = 0, D = 0, ld = 0, n = 0, n_pad = 0, kernel = 0, RCmax = 1;
+  std::vector<int> leaf_off, clus_off;
+  int Ltot = 0, Ctot = 0;
+  DBuf<float> ptsk, ynodek, xb, xq, ynear, yfar, mom, momq, loc, lco;
+  DBuf<int32_t> near_rowptr, near_col, far_rowptr, far_col, counts;
+  DBuf<int> d_leaf_off, err;
+  DBuf<ProbF32> probs;
+  ProbF32* h_probs = nullptr;   // pinned
+  DBuf<int2> work;
+  std::vector<int> up_off, up_cnt, down_off, down_cnt;
+  size_t far_smem = 0;
+  struct Cls {
+    int RC, leaf_first, leaf_count, clus_first, clus_count;
+  };
+  std::vector<Cls> classes;
+  bool split = false;
+  double tune_ms[2] = {0, 0};
+  cudaStream_t stream = nullptr, side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_copy = nullptr;
+  bool copied = false;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+
+  void release() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (h_probs) cudaFreeHost(h_probs);
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
+    if (ev_copy) cudaEventDestroy(ev_copy);
+    if (stream) cudaStreamDestroy(stream);
+    if (side) cudaStreamDestroy(side);
+    exec = nullptr;
+    graph = nullptr;
+    h_probs = nullptr;
+    ev_fork = ev_join = ev_copy = nullptr;
+    stream = side = nullptr;
+  }
+};
+
+namespace {
+
+SumArgs p2p_args(Batch& B, int RC, int leaf_first) {
+  SumArgs a{};
+  a.tgt = B.ptsk.p;
+  a.tgt_gstride = static_cast<int64_t>(B.D + 1) * B.ld;
+  a.src = B.ptsk.p;
+  a.src_gstride = a.tgt_gstride;
+  a.q = B.xq.p;   // class regions are disjoint: [leaf_first*ld*RC, (leaf_first+count)*ld*RC)
+  a.q_gstride = static_cast<int64_t>(RC) * B.ld;
+  a.out = B.ynear.p;
+  a.out_gstride = static_cast<int64_t>(kRC) * B.ld;
+  a.rowptr = B.near_rowptr.p;
+  a.col = B.near_col.p;
+  a.count = B.counts.p;
+  a.count_off = 0;
+  a.count_const = 0;
+  a.first = leaf_first;
+  a.ld = B.ld;
+  a.Rc = RC;
+  a.err = B.err.p;
+  return a;
+}
+
+SumArgs m2l_args(Batch& B, int RC, int clus_first) {
+  SumArgs a{};
+  a.tgt = B.ynodek.p;
+  a.tgt_gstride = static_cast<int64_t>(B.D + 1) * B.n_pad;
+  a.src = B.ynodek.p;
+  a.src_gstride = a.tgt_gstride;
+  a.q = B.momq.p;
+  a.q_gstride = static_cast<int64_t>(RC) * B.n_pad;
+  a.out = B.loc.p;
+  a.out_gstride = static_cast<int64_t>(kRC) * B.n_pad;
+  a.rowptr = B.far_rowptr.p;
+  a.col = B.far_col.p;
+  a.count = nullptr;
+  a.count_off = 0;
+  a.count_const = B.n;
+  a.first = clus_first;
+  a.ld = B.n_pad;
+  a.Rc = RC;
+  a.err = B.err.p;
+  return a;
+}
+
+int threads_for(int ld) { return std::min(128, round_up((ld + 1) / 2, 32)); }
+
+// The fused near-field work: interleave charges, P2P launch(es).
+void enqueue_near(Batch& B, bool split, cudaStream_t s) {
+  if (!split) {
+    launch_interleave(B.xb.p, B.Ltot, B.ld, B.RCmax, B.xq.p, s);
+    launch_sum_f32(B.D, B.kernel, B.RCmax, p2p_args(B, B.RCmax, 0), B.Ltot, threads_for(B.ld),
+                   sum_stage_bytes(B.D, B.RCmax, B.ld), s);
+    return;
+  }
+  for (const auto& c : B.classes) {
+    launch_interleave(B.xb.p + static_cast<int64_t>(c.leaf_first) * kRC * B.ld, c.leaf_count, B.ld, c.RC,
+                      B.xq.p + static_cast<int64_t>(c.leaf_first) * B.ld * c.RC, s);
+    launch_sum_f32(B.D, B.kernel, c.RC, p2p_args(B, c.RC, c.leaf_first), c.leaf_count, threads_for(B.ld),
+                   sum_stage_bytes(B.D, c.RC, B.ld), s);
+  }
+}
+
+void enqueue_m2l(Batch& B, bool split, cudaStream_t s) {
+  if (!split) {
+    launch_interleave(B.mom.p, B.Ctot, B.n_pad, B.RCmax, B.momq.p, s);
+    launch_sum_f32(B.D, B.kernel, B.RCmax, m2l_args(B, B.RCmax, 0), B.Ctot, threads_for(B.n_pad),
+                   sum_stage_bytes(B.D, B.RCmax, B.n_pad), s);
+    return;
+  }
+  for (const auto& c : B.classes) {
+    launch_interleave(B.mom.p + static_cast<int64_t>(c.clus_first) * kRC * B.n_pad, c.clus_count, B.n_pad, c.RC,
+                      B.momq.p + static_cast<int64_t>(c.clus_first) * B.n_pad * c.RC, s);
+    launch_sum_f32(B.D, B.kernel, c.RC, m2l_args(B, c.RC, c.clus_first), c.clus_count, threads_for(B.n_pad),
+                   sum_stage_bytes(B.D, c.RC, B.n_pad), s);
+  }
+}
+
+void enqueue_matvec(Batch& B) {
+  cudaStream_t s = B.stream;
+  launch_gather_batched(B.probs.p, B.d_leaf_off.p, B.P, B.Ltot, B.ld, B.xb.p, s);
+  DW_CUDA(cudaEventRecord(B.ev_fork, s));
+  DW_CUDA(cudaStreamWaitEvent(B.side, B.ev_fork, 0));
+  enqueue_near(B, B.split, B.side);
+  DW_CUDA(cudaEventRecord(B.ev_join, B.side));
+  for (size_t h = 0; h < B.up_off.size(); ++h)
+    launch_moments_batched(B.probs.p, B.work.p + B.up_off[h], B.up_cnt[h], B.far_smem, s);
+  enqueue_m2l(B, B.split, s);
+  for (size_t j = 0; j < B.down_off.size(); ++j)
+    launch_downward_batched(B.probs.p, B.work.p + B.down_off[j], B.down_cnt[j], B.far_smem, s);
+  DW_CUDA(cudaStreamWaitEvent(s, B.ev_join, 0));
+  launch_scatter_batched(B.probs.p, B.d_leaf_off.p, B.P, B.Ltot, B.ld, B.ynear.p, B.yfar.p, s);
+  DW_CUDA(cudaGetLastError());
+}
+
+double time_shape(Batch& B, bool split) {
+  cudaEvent_t a, b;
+  DW_CUDA(cudaEventCreate(&a));
+  DW_CUDA(cudaEventCreate(&b));
+  float best = 1e30f;
+  for (int rep = 0; rep < 2; ++rep) {
+    DW_CUDA(cudaEventRecord(a, B.stream));
+    enqueue_near(B, split, B.stream);
+    enqueue_m2l(B, split, B.stream);
+    DW_CUDA(cudaEventRecord(b, B.stream));
+    DW_CUDA(cudaEventSynchronize(b));
+    float ms = 0.f;
+    DW_CUDA(cudaEventElapsedTime(&ms, a, b));
+    best = std::min(best, ms);
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return best;
+}
+
+}  // namespace
+
+void batch_create(Batch& B, Plan* const* plans, const int32_t* nrhs, int count) {
+  if (count < 1) fail(DWFMM_ERR_INVALID_ARG, "empty batch");
+  Plan& P0 = *plans[0];
+  for (int i = 0; i < count; ++i) {
+    Plan& p = *plans[i];
+    if (!p.have_tree || p.N == 0) fail(DWFMM_ERR_STATE, "every plan needs a non-empty tree");
+    if (p.prec == DWFMM_P_FP64) fail(DWFMM_ERR_INVALID_ARG, "batches run float32 plans");
+    if (p.kernel != P0.kernel || p.n != P0.n || p.m_pad != P0.m_pad)
+      fail(DWFMM_ERR_INVALID_ARG, "plans differ in kernel, |Lambda| or leaf block size");
+    if (sum_padded_dim(p.d) < 0) fail(DWFMM_ERR_INVALID_ARG, "batches need d <= 16");
+    if (nrhs[i] < 1 || nrhs[i] > kRC || nrhs[i] > p.max_rhs) fail(DWFMM_ERR_INVALID_ARG, "nrhs outside 1..16");
+  }
+  B.P = count;
+  B.order.resize(count);
+  std::iota(B.order.begin(), B.order.end(), 0);
+  std::stable_sort(B.order.begin(), B.order.end(),
+                   [&](int a, int b) { return sum_padded_rc(nrhs[a]) < sum_padded_rc(nrhs[b]); });
+  for (int i : B.order) {
+    B.plans.push_back(plans[i]);
+    B.R.push_back(nrhs[i]);
+  }
+  B.kernel = P0.kernel;
+  B.n = P0.n;
+  B.n_pad = P0.n_pad;
+  B.ld = P0.m_pad;
+  B.D = 0;
+  int lsum_max = 0, Rmax = 1;
+  for (int i = 0; i < count; ++i) {
+    B.D = std::max(B.D, sum_padded_dim(B.plans[i]->d));
+    lsum_max = std::max(lsum_max, B.plans[i]->lsum);
+    Rmax = std::max(Rmax, B.R[i]);
+  }
+  B.RCmax = sum_padded_rc(Rmax);
+  B.leaf_off.assign(count + 1, 0);
+  B.clus_off.assign(count + 1, 0);
+  for (int i = 0; i < count; ++i) {
+    B.leaf_off[i + 1] = B.leaf_off[i] + B.plans[i]->L;
+    B.clus_off[i + 1] = B.clus_off[i] + B.plans[i]->C;
+  }
+  B.Ltot = B.leaf_off[count];
+  B.Ctot = B.clus_off[count];
+  DW_CUDA(cudaStreamCreateWithFlags(&B.stream, cudaStreamNonBlocking));
+  DW_CUDA(cudaStreamCreateWithFlags(&B.side, cudaStreamNonBlocking));
+  DW_CUDA(cudaEventCreateWithFlags(&B.ev_fork, cudaEventDisableTiming));
+  DW_CUDA(cudaEventCreateWithFlags(&B.ev_join, cudaEventDisableTiming));
+  DW_CUDA(cudaEventCreateWithFlags(&B.ev_copy, cudaEventDisableTiming));
+  cudaStream_t s = B.stream;
+  const size_t nl = static_cast<size_t>(B.Ltot) * kRC * B.ld;
+  const size_t nc = static_cast<size_t>(B.Ctot) * kRC * B.n_pad;
+  B.ptsk.alloc(static_cast<size_t>(B.Ltot) * (B.D + 1) * B.ld);
+  B.ynodek.alloc(static_cast<size_t>(B.Ctot) * (B.D + 1) * B.n_pad);
+  B.xb.alloc(nl);
+  B.ynear.alloc(nl);
+  B.yfar.alloc(nl);
+  B.xq.alloc(static_cast<size_t>(B.Ltot) * B.ld * B.RCmax);
+  B.mom.alloc(nc);
+  B.loc.alloc(nc);
+  B.lco.alloc(nc);
+  B.momq.alloc(static_cast<size_t>(B.Ctot) * B.n_pad * B.RCmax);
+  B.err.alloc(1);
+  DW_CUDA(cudaMemsetAsync(B.err.p, 0, sizeof(int), s));
+  DW_CUDA(cudaMemsetAsync(B.xb.p, 0, nl * sizeof(float), s));
+  DW_CUDA(cudaMemsetAsync(B.mom.p, 0, nc * sizeof(float), s));
+  // scaled blocks at the common padded dimension; global CSR lists
+  std::vector<int32_t> nr(B.Ltot + 1, 0), fr(B.Ctot + 1, 0), ncol, fcol, cnt(B.Ltot);
+  for (int i = 0; i < count; ++i) {
+    Plan& p = *B.plans[i];
+    launch_scaled_blocks(p.d_pts64.p, p.L, p.d, B.D, B.ld, B.kernel, p.sigma,
+                         B.ptsk.p + static_cast<size_t>(B.leaf_off[i]) * (B.D + 1) * B.ld, s);
+    launch_scaled_blocks(p.d_ynode64.p, p.C, p.d, B.D, B.n_pad, B.kernel, p.sigma,
+                         B.ynodek.p + static_cast<size_t>(B.clus_off[i]) * (B.D + 1) * B.n_pad, s);
+    std::vector<int32_t> rp(p.L + 1), cl(std::max<int64_t>(p.nnear, 1)), frp(p.C + 1), fcl(std::max<int64_t>(p.nfar, 1));
+    DW_CUDA(cudaMemcpy(rp.data(), p.d_near_rowptr.p, sizeof(int32_t) * (p.L + 1), cudaMemcpyDeviceToHost));
+    if (p.nnear) DW_CUDA(cudaMemcpy(cl.data(), p.d_near_col.p, sizeof(int32_t) * p.nnear, cudaMemcpyDeviceToHost));
+    DW_CUDA(cudaMemcpy(frp.data(), p.d_far_rowptr.p, sizeof(int32_t) * (p.C + 1), cudaMemcpyDeviceToHost));
+    if (p.nfar) DW_CUDA(cudaMemcpy(fcl.data(), p.d_far_col.p, sizeof(int32_t) * p.nfar, cudaMemcpyDeviceToHost));
+    for (int l = 0; l < p.L; ++l) {
+      nr[B.leaf_off[i] + l + 1] = rp[l + 1] - rp[l];
+      cnt[B.leaf_off[i] + l] = p.h_count[p.L - 1 + l];
+    }
+    for (int64_t e = 0; e < p.nnear; ++e) ncol.push_back(cl[e] + B.leaf_off[i]);
+    for (int c = 0; c < p.C; ++c) fr[B.clus_off[i] + c + 1] = frp[c + 1] - frp[c];
+    for (int64_t e = 0; e < p.nfar; ++e) fcol.push_back(fcl[e] + B.clus_off[i]);
+  }
+  for (int l = 0; l < B.Ltot; ++l) nr[l + 1] += nr[l];
+  for (int c = 0; c < B.Ctot; ++c) fr[c + 1] += fr[c];
+  B.near_rowptr.alloc(nr.size());
+  B.near_col.alloc(std::max<size_t>(ncol.size(), 1));
+  B.far_rowptr.alloc(fr.size());
+  B.far_col.alloc(std::max<size_t>(fcol.size(), 1));
+  B.counts.alloc(cnt.size());
+  DW_CUDA(cudaMemcpy(B.near_rowptr.p, nr.data(), sizeof(int32_t) * nr.size(), cudaMemcpyHostToDevice));
+  if (!ncol.empty()) DW_CUDA(cudaMemcpy(B.near_col.p, ncol.data(), sizeof(int32_t) * ncol.size(), cudaMemcpyHostToDevice));
+  DW_CUDA(cudaMemcpy(B.far_rowptr.p, fr.data(), sizeof(int32_t) * fr.size(), cudaMemcpyHostToDevice));
+  if (!fcol.empty()) DW_CUDA(cudaMemcpy(B.far_col.p, fcol.data(), sizeof(int32_t) * fcol.size(), cudaMemcpyHostToDevice));
+  DW_CUDA(cudaMemcpy(B.counts.p, cnt.data(), sizeof(int32_t) * cnt.size(), cudaMemcpyHostToDevice));
+  B.d_leaf_off.alloc(count + 1);
+  DW_CUDA(cudaMemcpy(B.d_leaf_off.p, B.leaf_off.data(), sizeof(int) * (count + 1), cudaMemcpyHostToDevice));
+  // problem table (pinned host copy: x/y pointers change per call)
+  DW_CUDA(cudaMallocHost(reinterpret_cast<void**>(&B.h_probs), sizeof(ProbF32) * count));
+  for (int i = 0; i < count; ++i) {
+    Plan& p = *B.plans[i];
+    ProbF32 q{};
+    q.e = p.exp_dev();
+    q.L = p.L;
+    q.J = p.J;
+    q.jmin = p.jmin;
+    q.m_pad = B.ld;
+    q.R = B.R[i];
+    q.count = p.d_count.p;
+    q.perm = p.d_perm.p;
+    q.begin = p.d_begin.p;
+    q.pts = p.d_pts32.p;
+    q.ynode = p.d_ynode32.p;
+    q.lo = p.d_lo32.p;
+    q.iext = p.d_iext32.p;
+    q.vinv = p.d_vinv32.p;
+    q.xb = B.xb.p + static_cast<size_t>(B.leaf_off[i]) * kRC * B.ld;
+    q.yfar = B.yfar.p + static_cast<size_t>(B.leaf_off[i]) * kRC * B.ld;
+    q.mom = B.mom.p + static_cast<size_t>(B.clus_off[i]) * kRC * B.n_pad;
+    q.loc = B.loc.p + static_cast<size_t>(B.clus_off[i]) * kRC * B.n_pad;
+    q.lco = B.lco.p + static_cast<size_t>(B.clus_off[i]) * kRC * B.n_pad;
+    q.x = nullptr;
+    q.y = nullptr;
+    q.ldx = q.ldy = p.N;
+    B.h_probs[i] = q;
+  }
+  B.probs.alloc(count);
+  DW_CUDA(cudaMemcpy(B.probs.p, B.h_probs, sizeof(ProbF32) * count, cudaMemcpyHostToDevice));
+  // work lists: upward by height above the leaves, downward by level
+  std::vector<int2> w;
+  int maxJ = 0;
+  for (auto* p : B.plans) maxJ = std::max(maxJ, p->J);
+  for (int h = 0; h <= maxJ; ++h) {
+    const int off = static_cast<int>(w.size());
+    for (int i = 0; i < count; ++i) {
+      Plan& p = *B.plans[i];
+      const int lev = p.J - h;
+      if (lev < 0 || lev < p.jmin) continue;
+      for (int g = (1 << lev) - 1; g < (1 << (lev + 1)) - 1; ++g) w.push_back(make_int2(i, g));
+    }
+    if (static_cast<int>(w.size()) > off) {
+      B.up_off.push_back(off);
+      B.up_cnt.push_back(static_cast<int>(w.size()) - off);
+    }
+  }
+  for (int j = 0; j <= maxJ; ++j) {
+    const int off = static_cast<int>(w.size());
+    for (int i = 0; i < count; ++i) {
+      Plan& p = *B.plans[i];
+      if (j < p.jmin || j > p.J) continue;
+      for (int g = (1 << j) - 1; g < (1 << (j + 1)) - 1; ++g) w.push_back(make_int2(i, g));
+    }
+    if (static_cast<int>(w.size()) > off) {
+      B.down_off.push_back(off);
+      B.down_cnt.push_back(static_cast<int>(w.size()) - off);
+    }
+  }
+  B.work.alloc(std::max<size_t>(w.size(), 1));
+  if (!w.empty()) DW_CUDA(cudaMemcpy(B.work.p, w.data(), sizeof(int2) * w.size(), cudaMemcpyHostToDevice));
+  B.far_smem = batch_far_smem(lsum_max, B.n_pad);
+  if (B.far_smem > 200 * 1024) fail(DWFMM_ERR_INVALID_ARG, "index sets too large for a batch");
+  batch_far_attrs();
+  ensure_sum_attrs();
+  // right-hand-side classes (contiguous in the internal order)
+  for (int i = 0; i < count;) {
+    const int rc = sum_padded_rc(B.R[i]);
+    int k = i;
+    while (k < count && sum_padded_rc(B.R[k]) == rc) ++k;
+    B.classes.push_back(Batch::Cls{rc, B.leaf_off[i], B.leaf_off[k] - B.leaf_off[i], B.clus_off[i],
+                                   B.clus_off[k] - B.clus_off[i]});
+    i = k;
+  }
+  DW_CUDA(cudaStreamSynchronize(s));
+  // autotune the P2P/M2L launch shape, then capture the whole matvec
+  B.tune_ms[0] = time_shape(B, false);
+  B.tune_ms[1] = B.classes.size() > 1 ? time_shape(B, true) : B.tune_ms[0];
+  B.split = B.classes.size() > 1 && B.tune_ms[1] < B.tune_ms[0];
+  DW_CUDA(cudaStreamBeginCapture(B.stream, cudaStreamCaptureModeThreadLocal));
+  enqueue_matvec(B);
+  DW_CUDA(cudaStreamEndCapture(B.stream, &B.graph));
+  DW_CUDA(cudaGraphInstantiate(&B.exec, B.graph, 0));
+}
+
+void batch_matvec(Batch& B, const double* const* x, double* const* y, cudaStream_t s) {
+  // the pinned table may still be the source of the previous call's copy
+  if (B.copied) DW_CUDA(cudaEventSynchronize(B.ev_copy));
+  for (int i = 0; i < B.P; ++i) {
+    const int c = B.order[i];
+    if (!x[c] || !y[c]) fail(DWFMM_ERR_INVALID_ARG, "NULL buffer in batch");
+    B.h_probs[i].x = x[c];
+    B.h_probs[i].y = y[c];
+  }
+  // the table lives in device memory; order it before the graph on the caller's stream
+  DW_CUDA(cudaMemcpyAsync(B.probs.p, B.h_probs, sizeof(ProbF32) * B.P, cudaMemcpyHostToDevice, s));
+  DW_CUDA(cudaEventRecord(B.ev_copy, s));
+  B.copied = true;
+  DW_CUDA(cudaGraphLaunch(B.exec, s));
+  DW_CUDA(cudaGetLastError());
+}
+
+}  // namespace dw
+
+namespace dw {
+
+Batch* batch_new() { return new Batch(); }
+void batch_delete(Batch* b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  b->release();
+  delete b;
+}
+void batch_info(const Batch& B, int32_t* split, double* tune_ms, int64_t* leaves) {
+  if (split) *split = B.split ? 1 : 0;
+  if (tune_ms) {
+    tune_ms[0] = B.tune_ms[0];
+    tune_ms[1] = B.tune_ms[1];
+  }
+  if (leaves) *leaves = B.Ltot;
+}
+
+}  // namespace dw

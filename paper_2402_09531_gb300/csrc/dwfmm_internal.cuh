@@ -99,6 +99,50 @@ struct ExpDev {
   const int32_t* loff;  // [d] offset of dimension k in a point's Legendre table
 };
 
+// One problem of a batch, float32 (device table entry).  Arrays marked
+// "slice" point into the batch's concatenated buffers.
+struct ProbF32 {
+  ExpDev e;
+  int L, J, jmin, m_pad, R;
+  const int32_t* count;   // [C] sites per cluster
+  const int32_t* perm;    // tree position -> caller index
+  const int32_t* begin;   // [C]
+  const float* pts;       // [L][d][m_pad]
+  const float* ynode;     // [C][d][n_pad]
+  const float* lo;        // [C][d]
+  const float* iext;      // [C][d]
+  const float* vinv;      // [n_pad][n_pad]
+  float* xb;              // slice [L][16][m_pad]
+  float* mom;             // slice [C][16][n_pad]
+  float* loc;             // slice
+  float* lco;             // slice
+  float* yfar;            // slice [L][16][m_pad]
+  const double* x;        // caller, column-major, ldx
+  double* y;
+  int64_t ldx, ldy;
+};
+
+// Arguments of the float32 kernel summation (P2P and M2L), see p2p_f32.cu.
+struct SumArgs {
+  const float* tgt;        // target blocks [g][D+1][ld] (scaled coords, norm row)
+  int64_t tgt_gstride;
+  const float* src;        // source blocks [g][D+1][ld]
+  int64_t src_gstride;
+  const float* q;          // charges [g][ld][RC] (interleaved per source)
+  int64_t q_gstride;
+  float* out;              // [g][16][ld]
+  int64_t out_gstride;
+  const int32_t* rowptr;   // CSR over target groups (indexed by first + blockIdx.x)
+  const int32_t* col;      // source group ids
+  const int32_t* count;    // group sizes (count[count_off + g]); nullptr -> count_const
+  int count_off;
+  int count_const;
+  int first;               // first target group
+  int ld;                  // m_pad or n_pad (multiple of 8)
+  int Rc;                  // right-hand sides actually written (<= RC)
+  int* err;
+};
+
 struct TreeDev {
   int64_t N;
   int J;
@@ -229,6 +273,36 @@ void launch_nearfield(Plan& P, int Rc, bool fp64, cudaStream_t s);
 bool p2p_f32_tuned(Plan& P, int Rc, cudaStream_t s);
 bool m2l_f32_tuned(Plan& P, int Rc);
 void check_device_error(Plan& P);
+// batches (batch.cu uses these)
+void batch_far_attrs();
+size_t batch_far_smem(int lsum, int n_pad);
+void launch_moments_batched(const ProbF32* probs, const int2* work, int items, size_t smem, cudaStream_t s);
+void launch_downward_batched(const ProbF32* probs, const int2* work, int items, size_t smem, cudaStream_t s);
+void launch_gather_batched(const ProbF32* probs, const int* leaf_off, int P, int Ltot, int ld, float* xb,
+                           cudaStream_t s);
+void launch_scatter_batched(const ProbF32* probs, const int* leaf_off, int P, int Ltot, int ld, const float* ynear,
+                            const float* yfar, cudaStream_t s);
+int sum_padded_dim(int d);
+int sum_padded_rc(int r);
+size_t sum_stage_bytes(int D, int RC, int ld);
+void launch_sum_f32(int D, int kernel, int RC, const SumArgs& a, int groups, int threads, size_t smem,
+                    cudaStream_t s);
+void launch_interleave(const float* src, int64_t groups, int ld, int RC, float* dst, cudaStream_t s);
+void launch_scaled_blocks(const double* src, int64_t groups, int d, int D, int ld, int kernel, double sigma,
+                          float* dst, cudaStream_t s);
+void ensure_sum_attrs();
+void evaluate(Plan& P, const double* tgt, int64_t nt, int64_t ldt, const double* c, int64_t ldc, double* out,
+              int64_t ldo, int R);
+void eval_f64(Plan& P, const double* tgt64, int G, const int32_t* rowptr, const int32_t* col, int Rc, double* out,
+              cudaStream_t s);
+void eval_f32(Plan& P, const double* tgt64, int G, const int32_t* rowptr, const int32_t* col, int Rc, float* out,
+              DBuf<float>& scratch, cudaStream_t s);
+struct Batch;
+Batch* batch_new();
+void batch_delete(Batch* b);
+void batch_create(Batch& B, Plan* const* plans, const int32_t* nrhs, int count);
+void batch_matvec(Batch& B, const double* const* x, double* const* y, cudaStream_t s);
+void batch_info(const Batch& B, int32_t* split, double* tune_ms, int64_t* leaves);
 dwfmm_status direct_sum_noalloc(int kernel, double sigma, const double* pts, int64_t n, int d, int64_t ldp,
                                 const double* x, double* y, int R, int64_t ldx, int64_t ldy,
                                 cudaStream_t s);
@@ -251,3 +325,7 @@ void timer_end(Plan& P, int phase, cudaStream_t s, int launches);
 void timers_collect(Plan& P);
 
 }  // namespace dw
+
+struct dwfmm_plan_s {
+  dw::Plan P;
+};

@@ -65,15 +65,13 @@ __device__ __forceinline__ void point_table(const ExpDev& e, const T* y, int64_t
 //  leaf mode:     sources = the leaf's sites, charges = right-hand sides.
 //  children mode: sources = nodes of both children, charges = their m.
 template <typename T>
-__global__ void __launch_bounds__(kFarThreads)
-k_moments(ExpDev e, int first, int leaf_mode, int L, const int32_t* count, const T* pts, int m_pad,
-          const T* xb, const T* ynode, const T* lo_all, const T* iext_all, const T* vinv, int Rc,
-          T* mom) {
+__device__ __forceinline__ void moments_body(const ExpDev& e, int g, int leaf_mode, int L, const int32_t* count,
+                                             const T* pts, int m_pad, const T* xb, const T* ynode,
+                                             const T* lo_all, const T* iext_all, const T* vinv, int Rc, T* mom) {
   extern __shared__ unsigned char smem_raw[];
   T* tab = reinterpret_cast<T*>(smem_raw);          // [kChunk][lsum]
   T* qs = tab + kChunk * e.lsum;                   // [kChunk][kRC]
   T* mu = qs + kChunk * kRC;                       // [n_pad][kRC]
-  const int g = first + blockIdx.x;
   const int n = e.n, np = e.n_pad, d = e.d;
   const T* lo = lo_all + static_cast<int64_t>(g) * d;
   const T* iext = iext_all + static_cast<int64_t>(g) * d;
@@ -147,19 +145,27 @@ k_moments(ExpDev e, int first, int leaf_mode, int L, const int32_t* count, const
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(kFarThreads)
+k_moments(ExpDev e, int first, int leaf_mode, int L, const int32_t* count, const T* pts, int m_pad,
+          const T* xb, const T* ynode, const T* lo_all, const T* iext_all, const T* vinv, int Rc,
+          T* mom) {
+  moments_body<T>(e, first + blockIdx.x, leaf_mode, L, count, pts, m_pad, xb, ynode, lo_all, iext_all, vinv,
+                  Rc, mom);
+}
+
 // Downward pass on cluster g = first + blockIdx.x (level `level`):
 //   l_g += B_g lambda_parent  (if level > jmin), lambda_g = V^{-1} l_g,
 //   and on the leaf level y_far = P_leaf lambda_leaf.
 template <typename T>
-__global__ void __launch_bounds__(kFarThreads)
-k_downward(ExpDev e, int first, int level, int jmin, int J, int L, const int32_t* count,
-           const T* pts, int m_pad, const T* ynode, const T* lo_all, const T* iext_all,
-           const T* loc, T* lco, const T* vinv, int Rc, T* yfar) {
+__device__ __forceinline__ void downward_body(const ExpDev& e, int g, int level, int jmin, int J, int L,
+                                              const int32_t* count, const T* pts, int m_pad, const T* ynode,
+                                              const T* lo_all, const T* iext_all, const T* loc, T* lco,
+                                              const T* vinv, int Rc, T* yfar) {
   extern __shared__ unsigned char smem_raw[];
   T* lamp = reinterpret_cast<T*>(smem_raw);        // [n_pad][kRC]
   T* lsm = lamp + e.n_pad * kRC;                  // [n_pad][kRC]
   T* tab = lsm + e.n_pad * kRC;                   // [kFarThreads][lsum]
-  const int g = first + blockIdx.x;
   const int n = e.n, np = e.n_pad, d = e.d;
   for (int idx = threadIdx.x; idx < np * kRC; idx += kFarThreads) {
     const int a = idx / kRC, r = idx % kRC;
@@ -233,6 +239,80 @@ k_downward(ExpDev e, int first, int level, int jmin, int J, int L, const int32_t
     }
     for (int r = 0; r < Rc; ++r) yfar[(static_cast<int64_t>(leaf) * kRC + r) * m_pad + i] = acc[r];
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kFarThreads)
+k_downward(ExpDev e, int first, int level, int jmin, int J, int L, const int32_t* count,
+           const T* pts, int m_pad, const T* ynode, const T* lo_all, const T* iext_all,
+           const T* loc, T* lco, const T* vinv, int Rc, T* yfar) {
+  downward_body<T>(e, first + blockIdx.x, level, jmin, J, L, count, pts, m_pad, ynode, lo_all, iext_all, loc,
+                   lco, vinv, Rc, yfar);
+}
+
+// ---- many problems in one launch (batches) --------------------------------
+// Work item = (problem, cluster); every problem's arrays come from its entry
+// of the problem table.
+
+__device__ __forceinline__ int level_of(int g) { return 31 - __clz(g + 1); }
+
+__global__ void __launch_bounds__(kFarThreads)
+k_moments_batched(const ProbF32* probs, const int2* work) {
+  const int2 w = work[blockIdx.x];
+  const ProbF32& p = probs[w.x];
+  moments_body<float>(p.e, w.y, level_of(w.y) == p.J, p.L, p.count, p.pts, p.m_pad, p.xb, p.ynode, p.lo, p.iext,
+                      p.vinv, p.R, p.mom);
+}
+
+__global__ void __launch_bounds__(kFarThreads)
+k_downward_batched(const ProbF32* probs, const int2* work) {
+  const int2 w = work[blockIdx.x];
+  const ProbF32& p = probs[w.x];
+  downward_body<float>(p.e, w.y, level_of(w.y), p.jmin, p.J, p.L, p.count, p.pts, p.m_pad, p.ynode, p.lo, p.iext,
+                       p.loc, p.lco, p.vinv, p.R, p.yfar);
+}
+
+// Problem of a global leaf (binary search in the leaf offsets).
+__device__ __forceinline__ int problem_of(const int* leaf_off, int P, int gl) {
+  int lo = 0, hi = P - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (leaf_off[mid] <= gl) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void k_gather_batched(const ProbF32* probs, const int* leaf_off, int P, int Ltot, int ld, float* xb) {
+  const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= static_cast<int64_t>(Ltot) * kRC * ld) return;
+  const int i = static_cast<int>(t % ld);
+  const int64_t lr = t / ld;
+  const int r = static_cast<int>(lr % kRC);
+  const int gl = static_cast<int>(lr / kRC);
+  const int pi = problem_of(leaf_off, P, gl);
+  const ProbF32& p = probs[pi];
+  const int c = p.L - 1 + (gl - leaf_off[pi]);
+  float v = 0.0f;
+  if (r < p.R && i < p.count[c]) v = static_cast<float>(p.x[static_cast<int64_t>(r) * p.ldx + p.perm[p.begin[c] + i]]);
+  xb[t] = v;
+}
+
+__global__ void k_scatter_batched(const ProbF32* probs, const int* leaf_off, int P, int Ltot, int ld,
+                                  const float* ynear, const float* yfar) {
+  const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= static_cast<int64_t>(Ltot) * kRC * ld) return;
+  const int i = static_cast<int>(t % ld);
+  const int64_t lr = t / ld;
+  const int r = static_cast<int>(lr % kRC);
+  const int gl = static_cast<int>(lr / kRC);
+  const int pi = problem_of(leaf_off, P, gl);
+  const ProbF32& p = probs[pi];
+  const int c = p.L - 1 + (gl - leaf_off[pi]);
+  if (r >= p.R || i >= p.count[c]) return;
+  double v = static_cast<double>(ynear[t]);
+  if (p.jmin <= p.J) v += static_cast<double>(yfar[t]);
+  p.y[static_cast<int64_t>(r) * p.ldy + p.perm[p.begin[c] + i]] = v;
 }
 
 // x (caller order, column-major) -> xb[leaf][r][m_pad] for r in [r0, r0+Rc).
@@ -370,6 +450,38 @@ void launch_scatter(Plan& P, double* y, int64_t ldy, int r0, int Rc, bool fp64) 
                                                                  P.d_count.p, P.L, P.m_pad, P.ynear32.p,
                                                                  P.yfar32.p, has_far);
   DW_CUDA(cudaGetLastError());
+}
+
+void batch_far_attrs() {
+  const int big = 200 * 1024;
+  DW_CUDA(cudaFuncSetAttribute(k_moments_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  DW_CUDA(cudaFuncSetAttribute(k_downward_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+}
+
+size_t batch_far_smem(int lsum, int n_pad) {
+  const size_t a = (static_cast<size_t>(kChunk) * lsum + kChunk * kRC + static_cast<size_t>(n_pad) * kRC) * 4;
+  const size_t b = (2 * static_cast<size_t>(n_pad) * kRC + static_cast<size_t>(kFarThreads) * lsum) * 4;
+  return std::max(a, b);
+}
+
+void launch_moments_batched(const ProbF32* probs, const int2* work, int items, size_t smem, cudaStream_t s) {
+  if (items > 0) k_moments_batched<<<items, kFarThreads, smem, s>>>(probs, work);
+}
+
+void launch_downward_batched(const ProbF32* probs, const int2* work, int items, size_t smem, cudaStream_t s) {
+  if (items > 0) k_downward_batched<<<items, kFarThreads, smem, s>>>(probs, work);
+}
+
+void launch_gather_batched(const ProbF32* probs, const int* leaf_off, int P, int Ltot, int ld, float* xb,
+                           cudaStream_t s) {
+  const int64_t total = static_cast<int64_t>(Ltot) * kRC * ld;
+  k_gather_batched<<<ceil_div(total, 256), 256, 0, s>>>(probs, leaf_off, P, Ltot, ld, xb);
+}
+
+void launch_scatter_batched(const ProbF32* probs, const int* leaf_off, int P, int Ltot, int ld, const float* ynear,
+                            const float* yfar, cudaStream_t s) {
+  const int64_t total = static_cast<int64_t>(Ltot) * kRC * ld;
+  k_scatter_batched<<<ceil_div(total, 256), 256, 0, s>>>(probs, leaf_off, P, Ltot, ld, ynear, yfar);
 }
 
 void launch_farfield(Plan& P, int Rc, bool fp64) {

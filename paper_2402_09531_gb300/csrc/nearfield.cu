@@ -34,36 +34,39 @@ struct Side {
   int count_const;   // used when count == nullptr
 };
 
-template <typename T, int KER>
+// DM: compile-time bound on d (coordinates beyond d are zero, so the extra
+// terms of the squared distance are exactly 0); RC: right-hand sides held in
+// registers (rows beyond Rc are zero charges).
+template <typename T, int KER, int DM, int RC>
 __global__ void __launch_bounds__(kThreads)
 k_ksum(int first_group, const int32_t* rowptr, const int32_t* col, int d, T inv_sigma,
        const T* tcoord, Side ts, const T* scoord, Side ss, const T* sq, int64_t sq_gstride,
        int sq_ld, T* out, int64_t o_gstride, int o_ld, int Rc) {
-  __shared__ T sc[kMaxDim * kSrcChunk];
-  __shared__ T sqs[kRC * kSrcChunk];
+  __shared__ T sc[DM * kSrcChunk];
+  __shared__ T sqs[RC * kSrcChunk];
   const int g = first_group + blockIdx.x;
   const int rb = rowptr[g], re = rowptr[g + 1];
   const int tcnt = ts.count ? ts.count[ts.count_off + g] : ts.count_const;
   for (int tb = 0; tb < ts.ld; tb += kThreads) {
     const int i = tb + threadIdx.x;
-    T xt[kMaxDim];
+    T xt[DM];
 #pragma unroll
-    for (int k = 0; k < kMaxDim; ++k)
+    for (int k = 0; k < DM; ++k)
       xt[k] = (k < d && i < tcnt) ? tcoord[g * ts.gstride + static_cast<int64_t>(k) * ts.ld + i] : T(0);
-    T acc[kRC];
+    T acc[RC];
 #pragma unroll
-    for (int r = 0; r < kRC; ++r) acc[r] = T(0);
+    for (int r = 0; r < RC; ++r) acc[r] = T(0);
     for (int e = rb; e < re; ++e) {
       const int s = col[e];
       const int scnt = ss.count ? ss.count[ss.count_off + s] : ss.count_const;
       for (int cb = 0; cb < scnt; cb += kSrcChunk) {
         const int cn = min(kSrcChunk, scnt - cb);
         __syncthreads();
-        for (int idx = threadIdx.x; idx < d * kSrcChunk; idx += kThreads) {
+        for (int idx = threadIdx.x; idx < DM * kSrcChunk; idx += kThreads) {
           const int k = idx / kSrcChunk, j = idx % kSrcChunk;
-          sc[idx] = j < cn ? scoord[s * ss.gstride + static_cast<int64_t>(k) * ss.ld + cb + j] : T(0);
+          sc[idx] = (j < cn && k < d) ? scoord[s * ss.gstride + static_cast<int64_t>(k) * ss.ld + cb + j] : T(0);
         }
-        for (int idx = threadIdx.x; idx < kRC * kSrcChunk; idx += kThreads) {
+        for (int idx = threadIdx.x; idx < RC * kSrcChunk; idx += kThreads) {
           const int r = idx / kSrcChunk, j = idx % kSrcChunk;
           sqs[idx] = (j < cn && r < Rc) ? sq[s * sq_gstride + static_cast<int64_t>(r) * sq_ld + cb + j] : T(0);
         }
@@ -71,22 +74,37 @@ k_ksum(int first_group, const int32_t* rowptr, const int32_t* col, int d, T inv_
         for (int j = 0; j < cn; ++j) {
           T r2 = T(0);
 #pragma unroll
-          for (int k = 0; k < kMaxDim; ++k) {
-            if (k < d) {
-              const T df = xt[k] - sc[k * kSrcChunk + j];
-              r2 += df * df;
-            }
+          for (int k = 0; k < DM; ++k) {
+            const T df = xt[k] - sc[k * kSrcChunk + j];
+            r2 += df * df;
           }
           const T ph = phi_r2<T, KER>(r2, inv_sigma);
 #pragma unroll
-          for (int r = 0; r < kRC; ++r) acc[r] += ph * sqs[r * kSrcChunk + j];
+          for (int r = 0; r < RC; ++r) acc[r] += ph * sqs[r * kSrcChunk + j];
         }
       }
     }
     if (i < o_ld) {
-      for (int r = 0; r < Rc; ++r) out[g * o_gstride + static_cast<int64_t>(r) * o_ld + i] = acc[r];
+#pragma unroll
+      for (int r = 0; r < RC; ++r)
+        if (r < Rc) out[g * o_gstride + static_cast<int64_t>(r) * o_ld + i] = acc[r];
     }
   }
+}
+
+template <typename T, int KER, int DM>
+void launch_ksum_rc(int ngroups, int first_group, const int32_t* rowptr, const int32_t* col, int d,
+                    T inv_sigma, const T* tcoord, Side ts, const T* scoord, Side ss, const T* sq,
+                    int64_t sq_gstride, int sq_ld, T* out, int64_t o_gstride, int o_ld, int Rc,
+                    cudaStream_t s) {
+#define DW_KS(RCV)                                                                                            \
+  k_ksum<T, KER, DM, RCV><<<ngroups, kThreads, 0, s>>>(first_group, rowptr, col, d, inv_sigma, tcoord, ts, \
+                                                       scoord, ss, sq, sq_gstride, sq_ld, out, o_gstride,   \
+                                                       o_ld, Rc)
+  if (Rc <= 1) DW_KS(1);
+  else if (Rc <= 4) DW_KS(4);
+  else DW_KS(16);
+#undef DW_KS
 }
 
 template <typename T, int KER>
@@ -95,9 +113,16 @@ void launch_ksum(int ngroups, int first_group, const int32_t* rowptr, const int3
                  int64_t sq_gstride, int sq_ld, T* out, int64_t o_gstride, int o_ld, int Rc,
                  cudaStream_t s) {
   if (ngroups <= 0) return;
-  k_ksum<T, KER><<<ngroups, kThreads, 0, s>>>(first_group, rowptr, col, d, inv_sigma, tcoord, ts,
-                                              scoord, ss, sq, sq_gstride, sq_ld, out, o_gstride,
-                                              o_ld, Rc);
+#define DW_KD(DMV)                                                                                 \
+  launch_ksum_rc<T, KER, DMV>(ngroups, first_group, rowptr, col, d, inv_sigma, tcoord, ts, scoord, \
+                              ss, sq, sq_gstride, sq_ld, out, o_gstride, o_ld, Rc, s)
+  if (d <= 4) DW_KD(4);
+  else if (d <= 8) DW_KD(8);
+  else if (d <= 12) DW_KD(12);
+  else if (d <= 16) DW_KD(16);
+  else if (d <= 20) DW_KD(20);
+  else DW_KD(kMaxDim);
+#undef DW_KD
 }
 
 template <typename T>
@@ -142,6 +167,17 @@ void p2p_impl(Plan& P, int Rc, const T* pts, const T* xb, T* ynear, cudaStream_t
 }
 
 }  // namespace
+
+// Every target block against every source leaf in float64 (exact evaluation).
+void eval_f64(Plan& P, const double* tgt64, int G, const int32_t* rowptr, const int32_t* col, int Rc, double* out,
+              cudaStream_t s) {
+  const int64_t gs = static_cast<int64_t>(P.d) * P.m_pad;
+  Side ts{gs, P.m_pad, nullptr, 0, P.m_pad};
+  Side ss{gs, P.m_pad, P.d_count.p, P.L - 1, 0};
+  dispatch_ksum<double>(P.kernel, G, 0, rowptr, col, P.d, 1.0 / P.sigma, tgt64, ts, P.d_pts64.p, ss, P.xb64.p,
+                        static_cast<int64_t>(kRC) * P.m_pad, P.m_pad, out, static_cast<int64_t>(kRC) * P.m_pad,
+                        P.m_pad, Rc, s);
+}
 
 void launch_m2l(Plan& P, int Rc, bool fp64) {
   if (P.jmin > P.J) return;

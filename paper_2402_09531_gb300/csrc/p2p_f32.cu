@@ -80,25 +80,6 @@ __device__ __forceinline__ float sqrt_approx(float x) {
   return y;
 }
 
-struct SumArgs {
-  const float* tgt;        // target blocks [g][D+1][ld] (scaled coords, norm row)
-  int64_t tgt_gstride;
-  const float* src;        // source blocks [g][D+1][ld]
-  int64_t src_gstride;
-  const float* q;          // charges [g][kRC][ld] (row r0 applied)
-  int64_t q_gstride;
-  float* out;              // [g][kRC][ld] (row r0 applied)
-  int64_t out_gstride;
-  const int32_t* rowptr;   // CSR over target groups (indexed by first + blockIdx.x)
-  const int32_t* col;      // source group ids
-  const int32_t* count;    // group sizes (count[count_off + g]); nullptr -> count_const
-  int count_off;
-  int count_const;
-  int first;               // first target group
-  int ld;                  // m_pad or n_pad (multiple of 8)
-  int Rc;                  // right-hand sides actually written (<= RC)
-  int* err;
-};
 
 template <int KER>
 __device__ __forceinline__ float phi_scaled(float a) {
@@ -425,6 +406,7 @@ int padded_dim(int d) {
   if (d <= 10) return 10;
   if (d <= 12) return 12;
   if (d <= 16) return 16;
+  if (d <= 20) return 20;
   return -1;
 }
 
@@ -436,7 +418,8 @@ void dispatch(int D, int kernel, int RC, SumArgs a, int groups, int threads, siz
     case 8: launch_rc<8>(kernel, RC, a, groups, threads, smem, s); break;
     case 10: launch_rc<10>(kernel, RC, a, groups, threads, smem, s); break;
     case 12: launch_rc<12>(kernel, RC, a, groups, threads, smem, s); break;
-    default: launch_rc<16>(kernel, RC, a, groups, threads, smem, s); break;
+    case 16: launch_rc<16>(kernel, RC, a, groups, threads, smem, s); break;
+    default: launch_rc<20>(kernel, RC, a, groups, threads, smem, s); break;
   }
 }
 
@@ -449,6 +432,7 @@ void ensure_attrs() {
   set_attrs<10>();
   set_attrs<12>();
   set_attrs<16>();
+  set_attrs<20>();
   DW_CUDA(cudaGetLastError());
   g_attrs_done = true;
 }
@@ -474,6 +458,27 @@ size_t stage_bytes(int D, int RC, int ld) {
 }
 
 }  // namespace
+
+int sum_padded_dim(int d) { return padded_dim(d); }
+int sum_padded_rc(int r) { return padded_rc(r); }
+size_t sum_stage_bytes(int D, int RC, int ld) { return stage_bytes(D, RC, ld); }
+void ensure_sum_attrs() { ensure_attrs(); }
+
+void launch_sum_f32(int D, int kernel, int RC, const SumArgs& a, int groups, int threads, size_t smem,
+                    cudaStream_t s) {
+  if (groups > 0) dispatch(D, kernel, RC, a, groups, threads, smem, s);
+}
+
+void launch_interleave(const float* src, int64_t groups, int ld, int RC, float* dst, cudaStream_t s) {
+  const int64_t nq = groups * ld * RC;
+  if (nq > 0) k_interleave<<<ceil_div(nq, 256), 256, 0, s>>>(src, groups, ld, RC, dst);
+}
+
+void launch_scaled_blocks(const double* src, int64_t groups, int d, int D, int ld, int kernel, double sigma,
+                          float* dst, cudaStream_t s) {
+  if (groups > 0)
+    k_scaled_blocks<<<ceil_div(groups * ld, 256), 256, 0, s>>>(src, groups, d, D, ld, kernel, sigma, dst);
+}
 
 bool p2p_f32_tuned(Plan& P, int Rc, cudaStream_t s) {
   const int D = padded_dim(P.d);
@@ -513,6 +518,44 @@ bool p2p_f32_tuned(Plan& P, int Rc, cudaStream_t s) {
   dispatch(D, P.kernel, RC, a, P.L, threads, smem, s);
   DW_CUDA(cudaGetLastError());
   return true;
+}
+
+// Every target block against every source leaf in float32 (exact evaluation);
+// falls back to the generic kernel when d > 20.
+void eval_f32(Plan& P, const double* tgt64, int G, const int32_t* rowptr, const int32_t* col, int Rc, float* out,
+              DBuf<float>& scratch, cudaStream_t s) {
+  const int D = padded_dim(P.d);
+  if (D < 0) fail(DWFMM_ERR_INVALID_ARG, "evaluation in float32 needs d <= 20");
+  const int RC = padded_rc(Rc);
+  ensure_attrs();
+  ensure_scaled(P, D);
+  scratch.alloc(static_cast<size_t>(G) * (D + 1) * P.m_pad);
+  k_scaled_blocks<<<ceil_div(static_cast<int64_t>(G) * P.m_pad, 256), 256, 0, s>>>(tgt64, G, P.d, D, P.m_pad, P.kernel,
+                                                                                  P.sigma, scratch.p);
+  P.xq32.alloc(static_cast<size_t>(P.L) * P.m_pad * kRC);
+  const int64_t nq = static_cast<int64_t>(P.L) * P.m_pad * RC;
+  k_interleave<<<ceil_div(nq, 256), 256, 0, s>>>(P.xb32.p, P.L, P.m_pad, RC, P.xq32.p);
+  SumArgs a{};
+  a.tgt = scratch.p;
+  a.tgt_gstride = static_cast<int64_t>(D + 1) * P.m_pad;
+  a.src = P.d_ptsk.p;
+  a.src_gstride = a.tgt_gstride;
+  a.q = P.xq32.p;
+  a.q_gstride = static_cast<int64_t>(RC) * P.m_pad;
+  a.out = out;
+  a.out_gstride = static_cast<int64_t>(kRC) * P.m_pad;
+  a.rowptr = rowptr;
+  a.col = col;
+  a.count = P.d_count.p;
+  a.count_off = P.L - 1;
+  a.count_const = 0;
+  a.first = 0;
+  a.ld = P.m_pad;
+  a.Rc = Rc;
+  a.err = P.d_err.p;
+  const int threads = std::min(kThreadsMax, round_up(ceil_div(P.m_pad, kTT), 32));
+  dispatch(D, P.kernel, RC, a, G, threads, stage_bytes(D, RC, P.m_pad), s);
+  DW_CUDA(cudaGetLastError());
 }
 
 bool m2l_f32_tuned(Plan& P, int Rc) {

@@ -188,17 +188,30 @@ dwfmm_status solve(Plan& P, double lam, const double* f, double* c, int R, int64
     delta.alloc(nr);
     rhs.alloc(nr);
     DW_CUDA(cudaMemcpyAsync(rhs.p, P.cg_f.p, nr * sizeof(double), cudaMemcpyDeviceToDevice, P.stream));
-    const double inner_tol = std::max(rtol, 1e-5);
+    // Each inner CG (float32 operator) reduces the float64 residual by at most
+    // 1e-3 within at most 400 iterations; the float64 residual then restarts
+    // it.  With a small ridge the float32 rounding of the operator (~1e-7 of
+    // ||K||) exceeds lambda, and one long float32 CG loses its way.
+    const double inner_floor = 1e-3;
+    const int inner_maxit = 400;
     status = DWFMM_ERR_NOT_CONVERGED;
-    for (int outer = 0; outer < 50 && total_it < maxit; ++outer) {
+    for (int outer = 0; outer < 100 && total_it < maxit; ++outer) {
       dots(P, rhs.p, rhs.p, n, n, R, V.part, V.dot, res2.data());
       bool done = true;
-      for (int r = 0; r < R; ++r) done &= std::sqrt(res2[r]) <= rtol * std::sqrt(fn2[r]) || fn2[r] == 0.0;
+      double relmax = 0.0;
+      for (int r = 0; r < R; ++r) {
+        const double rel = fn2[r] > 0.0 ? std::sqrt(res2[r] / fn2[r]) : 0.0;
+        done &= rel <= rtol;
+        relmax = std::max(relmax, rel);
+      }
       if (done) {
         status = DWFMM_OK;
         break;
       }
-      const int it = cg(P, V, rhs.p, delta.p, R, lam, inner_tol, maxit - total_it, false, st);
+      double inner_tol = std::max(rtol, 0.5 * rtol / std::max(relmax, 1e-300));
+      if (relmax > rtol / inner_floor) inner_tol = std::max(inner_tol, inner_floor);
+      inner_tol = std::min(0.5, inner_tol);
+      const int it = cg(P, V, rhs.p, delta.p, R, lam, inner_tol, std::min(inner_maxit, maxit - total_it), false, st);
       total_it += it;
       bool broke = false;
       for (int r = 0; r < R; ++r) broke |= st[r] == 1;

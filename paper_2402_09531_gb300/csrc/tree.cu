@@ -695,9 +695,11 @@ void build_cluster_data(Plan& P) {
   P.d_ynode32.alloc(ny);
   k_nodes<<<ceil_div(ny, 256), 256, 0, s>>>(P.d_lo.p, P.d_ext.p, P.d_nodes.p, C, d, P.n, P.n_pad,
                                             P.d_ynode64.p, P.d_ynode32.p);
+  // one block stride per leaf size (not per tree), so plans with equal leaf
+  // sizes share a layout and can be fused into one batch
   int maxleaf = 1;
   for (int l = 0; l < P.L; ++l) maxleaf = std::max(maxleaf, P.h_count[P.L - 1 + l]);
-  P.m_pad = round_up(maxleaf, 8);
+  P.m_pad = round_up(std::max(maxleaf, std::min<int>(P.leaf, static_cast<int>(std::max<int64_t>(P.N, 1)))), 8);
   const int64_t np = static_cast<int64_t>(P.L) * d * P.m_pad;
   P.d_pts64.alloc(std::max<int64_t>(np, 1));
   P.d_pts32.alloc(std::max<int64_t>(np, 1));

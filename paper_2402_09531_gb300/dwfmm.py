@@ -32,7 +32,9 @@ EXPORTS = ("dwfmm_plan_create", "dwfmm_plan_set_nodes", "dwfmm_tree_build", "dwf
            "dwfmm_solve", "dwfmm_plan_destroy", "dwfmm_status_string", "dwfmm_last_error",
            "dwfmm_plan_info", "dwfmm_plan_export", "dwfmm_tree_export", "dwfmm_lists_export",
            "dwfmm_set_profiling", "dwfmm_phase_times", "dwfmm_direct_sum_noalloc",
-           "dwfmm_cg_begin", "dwfmm_cg_step", "dwfmm_cg_poll", "dwfmm_cg_result", "dwfmm_residual")
+           "dwfmm_cg_begin", "dwfmm_cg_step", "dwfmm_cg_poll", "dwfmm_cg_result", "dwfmm_residual",
+           "dwfmm_batch_create", "dwfmm_batch_matvec", "dwfmm_batch_info", "dwfmm_batch_destroy",
+           "dwfmm_evaluate")
 
 
 class dwfmm_config(C.Structure):
@@ -77,6 +79,11 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "dwfmm_cg_poll": (i32, [P, C.POINTER(i32), P, P, P]),
         "dwfmm_cg_result": (i32, [P, P, i64, P]),
         "dwfmm_residual": (i32, [P, dbl, P, P, P, i32, i64, P, P]),
+        "dwfmm_batch_create": (i32, [P, P, i32, P, C.POINTER(P)]),
+        "dwfmm_batch_matvec": (i32, [P, P, P, P]),
+        "dwfmm_batch_info": (i32, [P, C.POINTER(i32), P, C.POINTER(i64)]),
+        "dwfmm_batch_destroy": (i32, [P]),
+        "dwfmm_evaluate": (i32, [P, P, i64, i64, P, i64, P, i64, i32, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -191,6 +198,18 @@ class Plan:
                                  C.byref(it), rel, _stream_handle(stream))
         return st, int(it.value), [float(v) for v in rel]
 
+    def evaluate(self, targets, c, out, stream=None):
+        """Interpolant at new points: out (R, nt) = sum_j phi(|t - x_j|) c (R, N)."""
+        nt = int(targets.shape[0])
+        ldt = int(targets.stride(0)) if hasattr(targets, "stride") and callable(targets.stride) else \
+            int(targets.strides[0] // 8)
+        R = int(c.shape[0])
+        ldc = int(c.stride(0)) if hasattr(c, "stride") and callable(c.stride) else int(c.strides[0] // 8)
+        ldo = int(out.stride(0)) if hasattr(out, "stride") and callable(out.stride) else int(out.strides[0] // 8)
+        self.check(self._l.dwfmm_evaluate(self.h, _ptr(targets), nt, ldt, _ptr(c), ldc, _ptr(out), ldo, R,
+                                          _stream_handle(stream)))
+        return out
+
     # -- incremental CG (many solves in flight) -----------------------------
     def cg_begin(self, lam: float, f, rtol: float = 1e-6, stream=None):
         """f: (R, N) float64 cuda tensor."""
@@ -268,3 +287,46 @@ class Plan:
         ln = np.zeros(7, dtype=np.int64)
         self.check(self._l.dwfmm_phase_times(self.h, ms.ctypes.data, ln.ctypes.data, 1 if reset else 0))
         return {p: (float(ms[i]), int(ln[i])) for i, p in enumerate(PHASES)}
+
+
+class Batch:
+    """Many uneven problems (float32 plans with built trees) in one fused matvec."""
+
+    def __init__(self, plans, nrhs, stream=None):
+        self._l = lib()
+        self.plans = list(plans)
+        self.nrhs = [int(r) for r in nrhs]
+        hs = (C.c_void_p * len(self.plans))(*[p.h.value for p in self.plans])
+        rs = (C.c_int32 * len(self.plans))(*self.nrhs)
+        h = C.c_void_p()
+        st = self._l.dwfmm_batch_create(hs, rs, len(self.plans), _stream_handle(stream), C.byref(h))
+        if st != OK:
+            msg = self._l.dwfmm_last_error(self.plans[0].h).decode()
+            raise DwfmmError(st, msg or self._l.dwfmm_status_string(st).decode())
+        self.h = h
+
+    def matvec(self, xs, ys, stream=None):
+        """xs[i], ys[i]: (nrhs_i, N_i) float64 cuda tensors (contiguous)."""
+        xp = (C.c_void_p * len(xs))(*[x.data_ptr() for x in xs])
+        yp = (C.c_void_p * len(ys))(*[y.data_ptr() for y in ys])
+        st = self._l.dwfmm_batch_matvec(self.h, xp, yp, _stream_handle(stream))
+        if st != OK:
+            raise DwfmmError(st, self._l.dwfmm_status_string(st).decode())
+
+    def info(self):
+        split = C.c_int32(0)
+        tune = (C.c_double * 2)()
+        leaves = C.c_int64(0)
+        self._l.dwfmm_batch_info(self.h, C.byref(split), tune, C.byref(leaves))
+        return {"split": bool(split.value), "tune_ms": [tune[0], tune[1]], "leaves": int(leaves.value)}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._l.dwfmm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -91,7 +91,8 @@ class Server:
     """Admission by memory and slots; all active solves advance concurrently."""
 
     def __init__(self, precision: str = "fp32", max_active: int = 8, mem_budget: int | None = None,
-                 step_iters: int = 8, device: int = 0):
+                 step_iters: int = 8, device: int = 0, inner_rtol: float | None = None,
+                 inner_maxit: int | None = None):
         import torch
         self.torch = torch
         self.dev = torch.device("cuda", device)
@@ -102,6 +103,11 @@ class Server:
             mem_budget = int(0.5 * free)
         self.mem_budget = mem_budget
         self.step_iters = step_iters
+        # float32 plans: each inner CG reduces the residual by inner_rtol at most
+        # inner_maxit iterations, then the float64 residual restarts it
+        # (iterative refinement); float64 plans run one CG to the tolerance.
+        self.inner_rtol = inner_rtol if inner_rtol is not None else (1e-3 if precision != "fp64" else None)
+        self.inner_maxit = inner_maxit if inner_maxit is not None else (400 if precision != "fp64" else None)
         self.pool: dict = {}
         self.used = 0
         self.peak_active = 0
@@ -137,7 +143,7 @@ class Server:
             f0 = torch.from_numpy(np.ascontiguousarray(r.f)).to(self.dev)
             acc = torch.zeros_like(f0)
         plan.tree_build(Xd, stream=stream)
-        plan.cg_begin(r.lam, f0, rtol=r.rtol, stream=stream)
+        plan.cg_begin(r.lam, f0, rtol=self._inner_tol(r.rtol, 1.0), stream=stream)
         plan.cg_step(self.step_iters, stream=stream)
         self.used += nbytes
         return _Active(r, plan, stream, key, f0, f0, acc, t_now, nbytes)
@@ -150,6 +156,15 @@ class Server:
         self._give_plan(a.key, a.plan)
         return Result(a.req.rid, c, status, a.iters, list(relres), a.refinements, a.req.arrival, a.t_admit, t_now)
 
+    def _inner_tol(self, rtol: float, relres: float) -> float:
+        """Relative tolerance of the next inner CG: enough to reach rtol from
+        the current float64 relative residual, never tighter than rtol itself,
+        and at most inner_rtol for float32 plans."""
+        need = max(rtol, 0.5 * rtol / max(relres, 1e-300))
+        if self.inner_rtol is not None:
+            need = max(need, self.inner_rtol) if relres > rtol / self.inner_rtol else need
+        return min(0.5, need)
+
     def _advance(self, a: _Active, t_now: float):
         """Handle a finished batch of iterations; returns a Result when done."""
         torch = self.torch
@@ -159,7 +174,8 @@ class Server:
         a_iters = int(its.max()) if len(its) else 0
         running = bool(np.any(st == 0))
         total = a.iters + a_iters
-        if running and total < a.req.maxit:
+        inner_cap = self.inner_maxit if self.inner_maxit is not None else a.req.maxit
+        if running and total < a.req.maxit and a_iters < inner_cap:
             a.plan.cg_step(self.step_iters, stream=a.stream)
             return None
         # inner solve finished: fold it into the accumulated solution
@@ -176,13 +192,12 @@ class Server:
         rel = a.plan.residual(a.req.lam, a.f0, a.acc, r=r, stream=a.stream)
         if np.all(rel <= a.req.rtol):
             return self._finish(a, "ok", rel, t_now)
-        if a.iters >= a.req.maxit or a.refinements >= 20:
+        if a.iters >= a.req.maxit or a.refinements >= 60:
             return self._finish(a, "not_converged", rel, t_now)
         # refinement: solve for the float64 residual, relative tolerance rtol of it
         a.refinements += 1
         a.fd = r
-        inner = min(0.5, max(1e-7, 0.5 * a.req.rtol / max(1e-300, float(np.max(rel)))))
-        a.plan.cg_begin(a.req.lam, r, rtol=inner, stream=a.stream)
+        a.plan.cg_begin(a.req.lam, r, rtol=self._inner_tol(a.req.rtol, float(np.max(rel))), stream=a.stream)
         a.plan.cg_step(self.step_iters, stream=a.stream)
         return None
 
