@@ -300,6 +300,27 @@ def run_ours(args):
     if not args.no_solve and rank == 0:
         solve = run_solve_sample(args)
 
+    fp64 = None
+    if args.compare_fp64 and rank == 0:
+        # the plain float64 GPU DW-FMM on the same workload (one step)
+        p64 = Plan(d=d, kernel=w.kernel, sigma=w.sigma, gamma=w.gamma, q=w.q, eta=w.eta, leaf_size=w.leaf,
+                   precision="fp64", max_rhs=R)
+        p64.tree_build(Xd)
+        y64 = torch.empty_like(xd)
+        p64.matvec(xd, y64)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        p64.matvec(xd, y64)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms64 = a.elapsed_time(b)
+        plan.matvec(xd, yd)
+        torch.cuda.synchronize()
+        rel = float(torch.max(torch.linalg.norm(yd - y64, dim=1) / torch.linalg.norm(y64, dim=1)))
+        fp64 = {"fp64_ms_per_step": ms64, "speedup_vs_fp64": ms64 / ms_max, "max_rel_diff_vs_fp64": rel}
+        p64.close()
+
     cpu = None
     if cpu_proc is not None:
         res = finish_oracle_subprocess(cpu_proc)
@@ -336,6 +357,7 @@ def run_ours(args):
             "clocks": clk.summary(), "clocks_e2e": clk2.summary(),
             "cpu_baseline": cpu,
             "solve": solve,
+            "fp64_comparison": fp64,
         }
         print(json.dumps(line), flush=True)
     plan.close()
@@ -418,6 +440,8 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=2)
     ap.add_argument("--n", type=int, default=0, help="override N (smaller case for profiling)")
     ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--compare-fp64", action="store_true",
+                    help="also time one float64 matvec of the same workload (about a minute at N=2^20)")
     ap.add_argument("--solve-requests", type=int, default=8)
     ap.add_argument("--solve-nmax", type=int, default=3000)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -1,0 +1,31 @@
+"""The Sec. 6.2 accuracy study through the library, at a small size.
+
+Sec. 6.2 describes the compression error over the sigma grid: very small for
+small length scales (the kernel matrix is nearly diagonal and the far field
+vanishes), rising to a maximum, then falling as the kernel becomes smooth
+away from the diagonal.  The prediction errors it reports are of order 1e-3
+to 1e-2 at the best parameters; at this size the test only requires a
+converged solve and a prediction error below 1.
+"""
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__ as ge
+    ge.build()
+
+
+def test_compression_error_rises_then_falls_over_sigma():
+    from paper_2402_09531_gb300 import accuracy
+    res = accuracy.study(n=6000, r=2.0, n_sigma=7, lambdas=[1e-3], n_cols=48, n_test=300, leaf=64,
+                         maxit=1500, seed=1)
+    ce = [row["ce_mean"] for row in res["rows"]]
+    k = max(range(len(ce)), key=lambda i: ce[i])
+    assert 0 < k < len(ce) - 1, ce            # the maximum is inside the sigma grid
+    assert ce[0] < 1e-2 * ce[k], ce           # nearly diagonal kernel: tiny far field
+    assert ce[-1] < ce[k], ce
+    best = min(row["pe"][1e-3]["pe"] for row in res["rows"])
+    assert best < 1.0
