@@ -283,18 +283,22 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_t = float(t.item())
 
-    # roofline of the dominant kernel (P2P): algorithmic FP32 flops per launch
+    # roofline of the dominant kernel (P2P): algorithmic FP32 flops per launch.
+    # MIXED plans with 9..16 RHS contract on the tensor cores (k_sum_tc): the
+    # CUDA cores then carry the kernel evaluation (3d + 4 flops per pair) and
+    # the 2R flops of the contraction run on the tensor pipe.
     p2p_ms, p2p_launches = phases["p2p"]
     p2p_avg_ms = p2p_ms / max(1, p2p_launches)
-    flops_pair = 3 * d + 4 + 2 * R
+    tensor_contraction = args.precision == "mixed" and 8 < R <= 16
+    flops_pair = 3 * d + 4 + (0 if tensor_contraction else 2 * R)
     achieved = pairs * flops_pair / (p2p_avg_ms / 1e3) / 1e12
     peaks = measured_peaks()
     clock_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     peak = SMS * FP32_LANES * 2 * clock_mhz * 1e6 / 1e12
     launches = sum(v[1] for k, v in phases.items() if k != "matvec")
-    # DRAM bytes per P2P launch from one ncu capture of this kernel version at this
-    # workload (profiles/p2p_k_sum_f32_gauss_d10.md); None for any other workload.
-    traffic = 14.84e9 if (args.workload == "mixed" and not args.n and args.precision != "fp64") else None
+    # DRAM bytes per P2P launch from an ncu capture of the current kernel version
+    # (profiles/); None where no capture of this kernel at this workload exists.
+    traffic = None
 
     solve = None
     if not args.no_solve and rank == 0:
@@ -346,9 +350,14 @@ def run_ours(args):
             "e2e": {"value": world * N * R / e2e_t, "unit": UNIT, "h2d_bytes_per_step": int(xh.numel() * 8),
                     "d2h_bytes_per_step": int(yh.numel() * 8)},
             "gpu_launches": int(launches),
-            "roofline": {"kernel": "p2p (near field)", "bound": "alu", "achieved": achieved, "peak": peak,
+            "roofline": {"kernel": ("p2p (near field): k_sum_tc, kernel evaluation on the FP32 pipe, "
+                                    "contraction on tcgen05 TF32 (counted separately below)") if tensor_contraction
+                         else "p2p (near field): k_sum_f32",
+                         "bound": "alu", "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                          "flops_per_pair": flops_pair, "pairs_per_launch": pairs,
+                         "tensor_flops_per_pair": (3 * 2 * 16) if tensor_contraction else 0,
+                         "tensor_tflops": (pairs * 96 / (p2p_avg_ms / 1e3) / 1e12) if tensor_contraction else 0.0,
                          "launch_ms": p2p_avg_ms,
                          "peak_basis": f"{SMS} SMs x {FP32_LANES} FP32 lanes x 2 flop x {clock_mhz:.0f} MHz"},
             "phase_ms_per_step": {k: v[0] / args.steps for k, v in phases.items()},

@@ -61,6 +61,7 @@ void Plan::free_tree() {
   d_ynodek.release();
   xq32.release();
   momq32.release();
+  bq32.release();
   dpad = -1;
 }
 

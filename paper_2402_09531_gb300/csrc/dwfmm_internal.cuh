@@ -236,6 +236,7 @@ struct Plan {
   int dpad = -1;
   DBuf<float> d_ptsk, d_ynodek;
   DBuf<float> xq32, momq32;   // charges interleaved per source, [g][ld][RC]
+  DBuf<float> bq32;           // TF32 hi/lo charge blocks for the tensor-core P2P
   cudaEvent_t ev_scaled = nullptr;
   DBuf<int> d_err;   // device error flag (3 = a bounded wait timed out)
 
@@ -291,6 +292,10 @@ void launch_interleave(const float* src, int64_t groups, int ld, int RC, float* 
 void launch_scaled_blocks(const double* src, int64_t groups, int d, int D, int ld, int kernel, double sigma,
                           float* dst, cudaStream_t s);
 void ensure_sum_attrs();
+bool sum_tc(int D, int kernel, const float* tgt, int64_t tgt_gstride, const float* src, int64_t src_gstride,
+            const float* xq16, int64_t groups_src, DBuf<float>& bq_scratch, float* out, int64_t out_gstride,
+            const int32_t* rowptr, const int32_t* col, const int32_t* count, int count_off, int count_const,
+            int first, int ngroups, int ld, int Rc, int* err, cudaStream_t s);
 void evaluate(Plan& P, const double* tgt, int64_t nt, int64_t ldt, const double* c, int64_t ldc, double* out,
               int64_t ldo, int R);
 void eval_f64(Plan& P, const double* tgt64, int G, const int32_t* rowptr, const int32_t* col, int Rc, double* out,

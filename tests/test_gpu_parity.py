@@ -346,3 +346,24 @@ def test_solve_through_negative_curvature_like_the_oracle():
     c = cd.cpu().numpy()[0]
     res = f[0] - (o.fmm_matvec(pb, c[None])[0] + 0.5 * c)
     assert np.linalg.norm(res) / np.linalg.norm(f[0]) <= 1e-7
+
+
+# ---------------------------------------------------------------------------
+# MIXED plans: near field with the contraction on the tensor cores (9..16 RHS)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("kernel", ["exp", "matern32", "gauss"])
+@pytest.mark.parametrize("n,nrhs,leaf", [(3001, 16, 64), (5000, 12, 256)])
+def test_mixed_tensor_core_near_field_matches_oracle(kernel, n, nrhs, leaf):
+    w, X, f, pb = _case("small", n, seed=31, kernel=kernel, nrhs=nrhs, leaf=leaf)
+    _, y = _gpu_matvec(w, X, f, pb, "mixed")
+    assert np.all(np.isfinite(y))
+    assert o.rel_err(y, o.fmm_matvec(pb, f)) <= FP32_TOL
+    _, y32 = _gpu_matvec(w, X, f, pb, "fp32")
+    assert o.rel_err(y, y32) <= FP32_TOL
+
+
+def test_mixed_tensor_core_d10_workload_shape():
+    w, X, f, pb = _case("mixed", 8192, seed=3, leaf=256, nrhs=16)
+    _, y = _gpu_matvec(w, X, f, pb, "mixed")
+    assert o.rel_err(y, o.fmm_matvec(pb, f)) <= FP32_TOL
