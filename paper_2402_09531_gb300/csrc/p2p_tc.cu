@@ -26,17 +26,18 @@
 #include <cstdint>
 
 #include "dwfmm_internal.cuh"
+#include "tcgen05_util.cuh"
 
 namespace dw {
 
 namespace {
 
+using namespace tc;
+
 constexpr int kCompWarps = 8;
 constexpr int kTcThreads = (kCompWarps + 2) * 32;   // compute warps, MMA warp, TMA warp
 constexpr int kChunkS = 32;                          // sources per A buffer
 constexpr int kTmemCols = 256;
-constexpr int kTcWait = 1 << 22;         // try_wait polls
-constexpr int kCtlPolls = 1 << 24;       // test_wait polls of the MMA and TMA threads
 // Sleeps of the MMA and TMA threads between polls: a longer first sleep
 // (about half of a chunk's, or of a block's, evaluation time), then short
 // steps, so that the control threads take few issue slots from the compute
@@ -44,56 +45,6 @@ constexpr int kCtlPolls = 1 << 24;       // test_wait polls of the MMA and TMA t
 constexpr uint32_t kMmaFirstNs = 384, kMmaStepNs = 96;
 constexpr uint32_t kTmaFirstNs = 2000, kTmaStepNs = 250;
 constexpr int kRow = 256;                // shared-memory row stride (floats) of the coordinates
-
-__device__ __forceinline__ uint32_t sptr(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
-
-// Bounded waits (a few seconds at most): try_wait polls for the compute
-// warps, test-and-sleep for the control threads.
-__device__ __forceinline__ bool wait_parity(uint64_t* bar, uint32_t parity) {
-  const uint32_t a = sptr(bar);
-  for (int it = 0; it < kTcWait; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(done)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
-}
-
-__device__ __forceinline__ bool test_parity(uint64_t* bar, uint32_t parity) {
-  uint32_t done;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(done)
-      : "r"(sptr(bar)), "r"(parity)
-      : "memory");
-  return done != 0;
-}
-
-// Wait of a control thread: test, sleep first_ns, then test every step_ns.
-__device__ __forceinline__ bool wait_ctl(uint64_t* bar, uint32_t parity, uint32_t first_ns, uint32_t step_ns) {
-  if (test_parity(bar, parity)) return true;
-  __nanosleep(first_ns);
-  for (int it = 0; it < kCtlPolls; ++it) {
-    if (test_parity(bar, parity)) return true;
-    __nanosleep(step_ns);
-  }
-  return false;
-}
-
-__device__ __forceinline__ float ex2f(float x) {
-  float y;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-__device__ __forceinline__ float sqrtf_a(float x) {
-  float y;
-  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
 
 template <int KER>
 __device__ __forceinline__ float phi_of(float a) {
@@ -104,66 +55,8 @@ __device__ __forceinline__ float phi_of(float a) {
   return fmaf(r, e, e);
 }
 
-typedef unsigned long long u64;
-__device__ __forceinline__ u64 pk(float a, float b) {
-  u64 r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-  return r;
-}
-__device__ __forceinline__ void up(u64 v, float& a, float& b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v)); }
-__device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c) {
-  u64 d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
-__device__ __forceinline__ u64 sub2(u64 a, u64 b) {
-  u64 d;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-
-// TF32 split: hi = value with the low 13 mantissa bits cleared (what the
-// MMA reads of a TF32 operand), lo = value - hi (exact, |lo| < 2^-10 |value|);
-// the MMA reads the top 19 bits of lo, so hi + lo carries ~2^-20 relative.
-__device__ __forceinline__ void split_tf32(float v, uint32_t& hi, uint32_t& lo) {
-  const uint32_t h = __float_as_uint(v) & 0xFFFFE000u;
-  hi = h;
-  lo = __float_as_uint(v - __uint_as_float(h));
-}
-
-// Instruction descriptor: D F32, A/B TF32, both K-major, N = 16, M = 128.
-constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
-
-// Shared-memory descriptor of a no-swizzle K-major operand: LBO = distance
-// between core matrices along K, SBO = distance between 8-row groups.
-__device__ __forceinline__ u64 smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-  return static_cast<u64>((addr >> 4) & 0x3FFF) | (static_cast<u64>((lbo >> 4) & 0x3FFF) << 16) |
-         (static_cast<u64>((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
-}
-
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint32_t a_tmem, u64 bdesc, uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}" ::"r"(
-          d_tmem),
-      "r"(a_tmem), "l"(bdesc), "r"(kIdesc), "r"(accumulate));
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(sptr(bar))
-               : "memory");
-}
-
-__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t* v) {
-  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(v[0]),
-               "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]));
-}
-
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* r) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-               : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
+// Instruction descriptor: M = 128 targets, N = 16 right-hand sides.
+constexpr uint32_t kIdesc = idesc_tf32(128, 16);
 
 // Charges [g][ld][16] (interleaved per source) -> TF32 hi and lo blocks in
 // the K-major core layout: block g = [hi | lo], each 16 x ld, core (nb, kb)
@@ -250,9 +143,6 @@ __device__ __forceinline__ void eval8(const float* sc, int j, const u64* xt2, u6
   }
 }
 
-__device__ __forceinline__ void bar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sptr(bar)) : "memory");
-}
 
 template <int D, int KER>
 __global__ void __launch_bounds__(kTcThreads, (D <= 12 ? 2 : 1)) k_sum_tc(TcArgs a) {
@@ -390,9 +280,9 @@ __global__ void __launch_bounds__(kTcThreads, (D <= 12 ? 2 : 1)) k_sum_tc(TcArgs
               const u64 bhi = smem_desc(bq_addr + boff, 128, static_cast<uint32_t>(ld * 32));
               const u64 blo = smem_desc(bq_addr + static_cast<uint32_t>(16 * ld * 4) + boff, 128,
                                         static_cast<uint32_t>(ld * 32));
-              mma_tf32(d_tmem, a_tmem + ks, bhi, (c0 + ks) > 0 ? 1u : 0u);
-              mma_tf32(d_tmem, a_tmem + ks, blo, 1u);
-              mma_tf32(d_tmem, a_tmem + 32 + ks, bhi, 1u);
+              mma_tf32(d_tmem, a_tmem + ks, bhi, kIdesc, (c0 + ks) > 0 ? 1u : 0u);
+              mma_tf32(d_tmem, a_tmem + ks, blo, kIdesc, 1u);
+              mma_tf32(d_tmem, a_tmem + 32 + ks, bhi, kIdesc, 1u);
             }
             mma_commit(&aempty[ab]);
             ++chunk;
