@@ -296,9 +296,9 @@ def run_ours(args):
     clock_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     peak = SMS * FP32_LANES * 2 * clock_mhz * 1e6 / 1e12
     launches = sum(v[1] for k, v in phases.items() if k != "matvec")
-    # DRAM bytes per P2P launch from an ncu capture of the current kernel version
-    # (profiles/); None where no capture of this kernel at this workload exists.
-    traffic = None
+    # DRAM bytes per P2P launch from a 1-pass ncu capture of the current kernel at
+    # this workload (profiles/launches_bench_mixed_gauss_d10.md); None elsewhere.
+    traffic = 108.53e9 if (tensor_contraction and args.workload == "mixed" and not args.n) else None
 
     solve = None
     if not args.no_solve and rank == 0:
