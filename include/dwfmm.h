@@ -61,9 +61,12 @@ typedef enum {
 
 /* Arithmetic of the matvec.  FP64: every phase in float64.  FP32: near field
  * (P2P), couplings (M2L) and expansions in float32 with compensated
- * accumulation.  MIXED: FP32 plus the V^{-1} moment/local conversions on
- * tensor cores in BF16 with FP32 accumulation.  CG dot products and
- * vectors are float64 in every mode. */
+ * accumulation.  MIXED: FP32 with the near-field contraction (targets x
+ * sources x right-hand sides) on the tensor cores when 9..16 right-hand
+ * sides are passed: TF32 with a hi/lo split of both operands and three
+ * products (~2^-20 relative per term), FP32 accumulation, compensated
+ * fold per source block.  CG dot products and vectors are float64 in every
+ * mode. */
 typedef enum {
   DWFMM_P_FP64 = 0,
   DWFMM_P_FP32 = 1,
@@ -82,6 +85,20 @@ typedef enum {
   DWFMM_W_EXPLICIT = 2
 } dwfmm_weight_rule;
 
+/* Shape of the index set Lambda (the polynomial space of the expansion).
+ *  TOTAL_DEGREE: sum_k omega_k alpha_k <= q, the weighted total degree set
+ *                Lambda_{omega,q,d} of Sec. 4 (total degree interpolation
+ *                for omega = 1, Sec. 6.1).
+ *  TENSOR:       max_k omega_k alpha_k <= q, a tensor-product set; for
+ *                omega = 1 the set ||alpha||_inf <= q of (q+1)^d indices
+ *                that Sec. 6.1 compares against (tensor product
+ *                interpolation).  No counterpart in the paper for omega != 1
+ *                beyond the anisotropic reading of the same bound. */
+typedef enum {
+  DWFMM_I_TOTAL_DEGREE = 0,
+  DWFMM_I_TENSOR = 1
+} dwfmm_index_set;
+
 /* Plan parameters.  All fields are read during dwfmm_plan_create only. */
 typedef struct {
   int32_t d;                  /* dimension, 1..32 */
@@ -96,6 +113,7 @@ typedef struct {
   int32_t halton_candidates;  /* Halton candidates M; <= 0 selects max(2000, 10 n) (Sec. 5.4) */
   int32_t precision;          /* dwfmm_precision */
   int32_t max_rhs;            /* largest R passed to matvec/solve, 1..64 */
+  int32_t index_set;          /* dwfmm_index_set; 0 (TOTAL_DEGREE) for the paper's method */
 } dwfmm_config;
 
 typedef struct dwfmm_plan_s* dwfmm_plan;

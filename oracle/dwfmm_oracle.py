@@ -24,6 +24,7 @@ claims of Sec. 6.1 are pinned instead).
 """
 from __future__ import annotations
 
+import itertools
 import math
 from dataclasses import dataclass, field
 
@@ -91,14 +92,32 @@ def weights_inv_gamma(gamma) -> np.ndarray:
 # Weighted total-degree index set (Sec. 4, Lambda_{omega,q,d})
 # ---------------------------------------------------------------------------
 
-def index_set(w, q: float) -> np.ndarray:
-    """All alpha in N^d with sum_l omega_l alpha_l <= q (Sec. 4).
+def index_set(w, q: float, shape: str = "total") -> np.ndarray:
+    """All alpha in N^d with sum_l omega_l alpha_l <= q (Sec. 4), or, for
+    shape "tensor", with max_l omega_l alpha_l <= q (the tensor-product set
+    ||alpha||_inf <= q of Sec. 6.1 when omega = 1).
 
     Reading: the comparison is inclusive with a relative slack of 1e-12
     (sum <= q (1 + 1e-12)); the sum is accumulated left to right in float64
     (s_k = s_{k-1} + omega_k alpha_k).  Enumeration order: lexicographic in
     (alpha_1, ..., alpha_d), alpha_1 most significant.
     """
+    if shape == "tensor":
+        w = [float(v) for v in w]
+        if any(not (v > 0.0) for v in w):
+            raise ValueError("weights must be positive")
+        tol = float(q) * (1.0 + 1e-12)
+        ranges = []
+        for v in w:                       # the a >= 0 with omega_k a <= q, one by one
+            a = 0
+            while v * float(a + 1) <= tol:
+                a += 1
+            ranges.append(range(a + 1))
+        # itertools.product varies the last index fastest: lexicographic order
+        out = [list(a) for a in itertools.product(*ranges)]
+        return np.array(out, dtype=np.int64).reshape(len(out), len(w))
+    if shape != "total":
+        raise ValueError("shape must be 'total' or 'tensor'")
     w = [float(v) for v in w]
     d = len(w)
     if any(not (v > 0.0) for v in w):
@@ -255,9 +274,9 @@ class Expansion:
 
 
 def make_expansion(weights, q: float, nodes: np.ndarray | None = None,
-                   M: int | None = None) -> Expansion:
+                   M: int | None = None, shape: str = "total") -> Expansion:
     """Index set, approximate Fekete nodes and Vandermonde matrix (Eq. (5.3))."""
-    Lam = index_set(weights, q)
+    Lam = index_set(weights, q, shape)
     n, d = Lam.shape
     pivots: list = []
     if nodes is None:
@@ -525,9 +544,9 @@ def problem_coefficient(pb: Problem, t: int, s: int) -> np.ndarray:
 
 
 def make_problem(X, kernel: str, weights, q: float, leaf: int, eta: float,
-                 sigma: float = 1.0, nodes=None) -> Problem:
+                 sigma: float = 1.0, nodes=None, shape: str = "total") -> Problem:
     X = np.asarray(X, dtype=np.float64)
-    exp_ = make_expansion(weights, q, nodes=nodes)
+    exp_ = make_expansion(weights, q, nodes=nodes, shape=shape)
     tree = build_tree(X, leaf)
     lists = build_lists(tree, eta)
     return Problem(X, kernel, sigma, exp_, tree, lists)

@@ -62,6 +62,7 @@ void Plan::free_tree() {
   xq32.release();
   momq32.release();
   bq32.release();
+  bqm32.release();
   dpad = -1;
 }
 
@@ -187,6 +188,7 @@ dwfmm_status dwfmm_plan_create(const dwfmm_config* cfg, void* stream, dwfmm_plan
     if (cfg->leaf_size < 2 || cfg->leaf_size > 1024) fail(DWFMM_ERR_INVALID_ARG, "leaf_size must be in 2..1024");
     if (cfg->precision < 0 || cfg->precision > 2) fail(DWFMM_ERR_INVALID_ARG, "unknown precision");
     if (cfg->max_rhs < 1 || cfg->max_rhs > 64) fail(DWFMM_ERR_INVALID_ARG, "max_rhs must be in 1..64");
+    if (cfg->index_set < 0 || cfg->index_set > 1) fail(DWFMM_ERR_INVALID_ARG, "unknown index set");
     P.d = cfg->d;
     P.kernel = cfg->kernel;
     P.sigma = cfg->sigma;
@@ -201,6 +203,7 @@ dwfmm_status dwfmm_plan_create(const dwfmm_config* cfg, void* stream, dwfmm_plan
     P.M = cfg->halton_candidates;
     P.prec = cfg->precision;
     P.max_rhs = cfg->max_rhs;
+    P.iset = cfg->index_set;
     DW_CUDA(cudaGetDevice(&P.device));
     bind_stream(P, stream);
     DW_CUDA(cudaStreamCreateWithFlags(&P.side, cudaStreamNonBlocking));

@@ -181,6 +181,7 @@ struct CgState {
 struct Plan {
   // configuration
   int d = 0, kernel = 0, wrule = 0, leaf = 0, M = 0, prec = 0, max_rhs = 0;
+  int iset = 0;   // dwfmm_index_set
   double sigma = 1.0, q = 0.0, eta = 1.0;
   std::vector<double> gamma, w;
   cudaStream_t stream = nullptr;   // stream of the last call
@@ -237,6 +238,7 @@ struct Plan {
   DBuf<float> d_ptsk, d_ynodek;
   DBuf<float> xq32, momq32;   // charges interleaved per source, [g][ld][RC]
   DBuf<float> bq32;           // TF32 hi/lo charge blocks for the tensor-core P2P
+  DBuf<float> bqm32;          // the same for the tensor-core M2L (moments at the nodes)
   cudaEvent_t ev_scaled = nullptr;
   DBuf<int> d_err;   // device error flag (3 = a bounded wait timed out)
 

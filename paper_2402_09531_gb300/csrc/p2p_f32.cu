@@ -577,6 +577,14 @@ bool m2l_f32_tuned(Plan& P, int Rc) {
   P.momq32.alloc(static_cast<size_t>(P.C) * P.n_pad * kRC);
   const int64_t nq = static_cast<int64_t>(P.C) * P.n_pad * RC;
   k_interleave<<<ceil_div(nq, 256), 256, 0, P.stream>>>(P.mom32.p, P.C, P.n_pad, RC, P.momq32.p);
+  // MIXED plans with 9..16 right-hand sides: contraction on the tensor cores
+  // (own charge-block scratch: the near field runs concurrently on the side stream)
+  if (P.prec == DWFMM_P_MIXED && RC == 16 &&
+      sum_tc(D, P.kernel, P.d_ynodek.p, static_cast<int64_t>(D + 1) * P.n_pad, P.d_ynodek.p,
+             static_cast<int64_t>(D + 1) * P.n_pad, P.momq32.p, P.C, P.bqm32, P.loc32.p,
+             static_cast<int64_t>(kRC) * P.n_pad, P.d_far_rowptr.p, P.d_far_col.p, nullptr, 0, P.n, first,
+             P.C - first, P.n_pad, Rc, P.d_err.p, P.stream))
+    return true;
   SumArgs a{};
   a.tgt = P.d_ynodek.p;
   a.tgt_gstride = static_cast<int64_t>(D + 1) * P.n_pad;

@@ -138,8 +138,14 @@ __device__ __forceinline__ void eval8(const float* sc, int j, const u64* xt2, u6
   for (int u = 0; u < 4; ++u) {
     float f0, f1;
     up(p[u], f0, f1);
-    split_tf32(phi_of<KER>(f0), hi[2 * u], lo[2 * u]);
-    split_tf32(phi_of<KER>(f1), hi[2 * u + 1], lo[2 * u + 1]);
+    const float e0 = phi_of<KER>(f0), e1 = phi_of<KER>(f1);
+    const uint32_t h0 = __float_as_uint(e0) & 0xFFFFE000u, h1 = __float_as_uint(e1) & 0xFFFFE000u;
+    float l0, l1;
+    up(sub2(pk(e0, e1), pk(__uint_as_float(h0), __uint_as_float(h1))), l0, l1);
+    hi[2 * u] = h0;
+    hi[2 * u + 1] = h1;
+    lo[2 * u] = __float_as_uint(l0);
+    lo[2 * u + 1] = __float_as_uint(l1);
   }
 }
 
@@ -362,11 +368,17 @@ __global__ void __launch_bounds__(kTcThreads, (D <= 12 ? 2 : 1)) k_sum_tc(TcArgs
         const int j0 = c0 + 16 * hf;
         const int jn = min(16, s8 - j0);
         const uint32_t col = static_cast<uint32_t>(64 * ab + 16 * hf);
-        for (int sub = 0; sub < jn; sub += 8) {
+        if (jn >= 16) {
+          uint32_t hi[16], lo[16];
+          eval8<D, KER>(sc, j0, xt2, mnt2, hi, lo);
+          eval8<D, KER>(sc, j0 + 8, xt2, mnt2, hi + 8, lo + 8);
+          tmem_st16(lane_base + col, hi);
+          tmem_st16(lane_base + col + 32, lo);
+        } else if (jn > 0) {
           uint32_t hi[8], lo[8];
-          eval8<D, KER>(sc, j0 + sub, xt2, mnt2, hi, lo);
-          tmem_st8(lane_base + col + sub, hi);
-          tmem_st8(lane_base + col + 32 + sub, lo);
+          eval8<D, KER>(sc, j0, xt2, mnt2, hi, lo);
+          tmem_st8(lane_base + col, hi);
+          tmem_st8(lane_base + col + 32, lo);
         }
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;");

@@ -40,9 +40,11 @@ static std::vector<double> make_weights(const Plan& P) {
   return w;
 }
 
-// Lexicographic enumeration (alpha_1 most significant).  Partial sums are
-// accumulated left to right; the test is inclusive with a 1e-12 relative slack.
-static void enumerate(const std::vector<double>& w, double tol, int k, double s,
+// Lexicographic enumeration (alpha_1 most significant).  Total degree: the
+// partial sums s_k = s_{k-1} + omega_k alpha_k are accumulated left to right;
+// tensor: every term omega_k alpha_k alone is bounded.  The test is inclusive
+// with a 1e-12 relative slack.
+static void enumerate(const std::vector<double>& w, double tol, bool tensor, int k, double s,
                       std::vector<int32_t>& alpha, std::vector<int32_t>& out, size_t cap) {
   const int d = static_cast<int>(w.size());
   if (k == d) {
@@ -51,10 +53,11 @@ static void enumerate(const std::vector<double>& w, double tol, int k, double s,
     return;
   }
   for (int a = 0;; ++a) {
-    const double t = s + w[k] * static_cast<double>(a);
+    const double term = w[k] * static_cast<double>(a);
+    const double t = tensor ? term : s + term;
     if (t > tol) break;
     alpha[k] = a;
-    enumerate(w, tol, k + 1, t, alpha, out, cap);
+    enumerate(w, tol, tensor, k + 1, tensor ? 0.0 : t, alpha, out, cap);
   }
   alpha[k] = 0;
 }
@@ -65,7 +68,7 @@ static void make_index_set(Plan& P) {
     if (!(P.w[k] > 0.0) || !std::isfinite(P.w[k])) fail(DWFMM_ERR_INVALID_ARG, "weights must be positive");
   const double tol = P.q * (1.0 + 1e-12);
   std::vector<int32_t> alpha(P.d, 0), out;
-  enumerate(P.w, tol, 0, 0.0, alpha, out, 4096);
+  enumerate(P.w, tol, P.iset == DWFMM_I_TENSOR, 0, 0.0, alpha, out, 4096);
   P.lam = out;
   P.n = static_cast<int>(out.size() / P.d);
   P.n_pad = round_up(P.n, 8);

@@ -25,6 +25,8 @@ W_INV_GAMMA, W_PAPER_LOGRHO, W_EXPLICIT = 0, 1, 2
 KERNELS = {"exp": K_EXP, "matern32": K_MATERN32, "gauss": K_GAUSS}
 PRECISIONS = {"fp64": P_FP64, "fp32": P_FP32, "mixed": P_MIXED}
 WEIGHT_RULES = {"inv_gamma": W_INV_GAMMA, "paper_logrho": W_PAPER_LOGRHO, "explicit": W_EXPLICIT}
+I_TOTAL_DEGREE, I_TENSOR = 0, 1
+INDEX_SETS = {"total": I_TOTAL_DEGREE, "tensor": I_TENSOR}
 PHASES = ("gather", "p2m_m2m", "m2l", "l2l_l2p", "p2p", "scatter", "matvec")
 
 # Every entry point declared in include/dwfmm.h.
@@ -42,7 +44,7 @@ class dwfmm_config(C.Structure):
                 ("gamma", C.POINTER(C.c_double)), ("weight_rule", C.c_int32),
                 ("weights", C.POINTER(C.c_double)), ("q", C.c_double), ("eta", C.c_double),
                 ("leaf_size", C.c_int32), ("halton_candidates", C.c_int32),
-                ("precision", C.c_int32), ("max_rhs", C.c_int32)]
+                ("precision", C.c_int32), ("max_rhs", C.c_int32), ("index_set", C.c_int32)]
 
 
 class DwfmmError(RuntimeError):
@@ -129,7 +131,7 @@ class Plan:
     def __init__(self, d: int, kernel: str = "exp", sigma: float = 1.0, gamma=None,
                  weight_rule: str = "inv_gamma", weights=None, q: float = 4.0, eta: float = 1.0,
                  leaf_size: int = 64, halton_candidates: int = 0, precision: str = "fp64",
-                 max_rhs: int = 16, stream=None):
+                 max_rhs: int = 16, stream=None, index_set: str = "total"):
         self._l = lib()
         self.d = int(d)
         self.precision = precision
@@ -142,7 +144,7 @@ class Plan:
                            WEIGHT_RULES[weight_rule],
                            w.ctypes.data_as(C.POINTER(C.c_double)) if w is not None else None,
                            float(q), float(eta), int(leaf_size), int(halton_candidates),
-                           PRECISIONS[precision], self.max_rhs)
+                           PRECISIONS[precision], self.max_rhs, INDEX_SETS[index_set])
         h = C.c_void_p()
         st = self._l.dwfmm_plan_create(C.byref(cfg), _stream_handle(stream), C.byref(h))
         if st != OK:

@@ -367,3 +367,35 @@ def test_mixed_tensor_core_d10_workload_shape():
     w, X, f, pb = _case("mixed", 8192, seed=3, leaf=256, nrhs=16)
     _, y = _gpu_matvec(w, X, f, pb, "mixed")
     assert o.rel_err(y, o.fmm_matvec(pb, f)) <= FP32_TOL
+
+
+# ---------------------------------------------------------------------------
+# Tensor-product index set (Sec. 6.1's TPI) as a comparison mode
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("weights,q", [([1.0, 1.0, 1.0, 1.0], 2.0), ([1.0, 2.0, 4.0, 8.0], 4.0)])
+def test_tensor_index_set_expansion_and_matvec_match_oracle(weights, q):
+    from paper_2402_09531_gb300 import Plan
+    torch = _torch()
+    w = di.scaled(di.small_exp_d4(), 3001)
+    X, f = di.sites_and_rhs(w, nrhs=2)
+    wts = np.array(weights)
+    plan = Plan(d=w.d, kernel=w.kernel, sigma=w.sigma, gamma=w.gamma, weight_rule="explicit", weights=wts,
+                q=q, eta=w.eta, leaf_size=64, precision="fp64", max_rhs=2, index_set="tensor")
+    ex = plan.export_expansion()
+    lam = o.index_set(wts, q, "tensor")
+    assert np.array_equal(ex["lam"], lam)
+    oe = o.make_expansion(wts, q, shape="tensor")
+    ours, theirs = list(ex["pivots"]), list(oe.pivots)
+    if ours != theirs:
+        H = o.halton(o.halton_count(len(lam)), w.d)
+        assert _near_tie_ok(o.basis_eval(lam, H).T, theirs, ours)
+    pb = o.make_problem(X, w.kernel, wts, q, 64, w.eta, shape="tensor")
+    plan.set_nodes(pb.exp_.nodes)          # matvec parity separated from node-selection parity
+    plan.tree_build(torch.from_numpy(X).cuda())
+    xd = torch.from_numpy(f).cuda()
+    yd = torch.full_like(xd, float("nan"))
+    plan.matvec(xd, yd)
+    torch.cuda.synchronize()
+    assert o.rel_err(yd.cpu().numpy(), o.fmm_matvec(pb, f)) <= FP64_TOL
+    plan.close()

@@ -465,3 +465,51 @@ def test_vectorised_admissibility_equals_scalar_rule():
         vec = o.admissible_pairs(tr.lo, tr.hi, t, s, eta)
         ref = [o.admissible(tr.lo[a], tr.hi[a], tr.lo[b], tr.hi[b], eta) for a, b in zip(t, s)]
         assert vec.tolist() == ref
+
+
+# ---------------------------------------------------------------------------
+# Tensor-product index set (Sec. 6.1's TPI, max_k omega_k alpha_k <= q)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("d,q", [(1, 5), (2, 3), (3, 2), (4, 1), (5, 0)])
+def test_tensor_set_count_is_q_plus_one_to_the_d(d, q):
+    """Sec. 6.1: |{alpha : ||alpha||_inf <= q}| = (q+1)^d."""
+    lam = o.index_set(np.ones(d), q, "tensor")
+    assert lam.shape == (o.tensor_index_count(q, d), d) == ((q + 1) ** d, d)
+    assert len({tuple(a) for a in lam}) == len(lam)
+    assert lam.max(initial=0) <= q
+
+
+def test_tensor_set_anisotropic_count_and_order():
+    w, q = [1.0, 2.0, 0.7], 3.0
+    lam = o.index_set(w, q, "tensor")
+    # per coordinate the a >= 0 with omega_k a <= q: 0..3, 0..1, 0..4
+    assert len(lam) == 4 * 2 * 5
+    assert [tuple(a) for a in lam] == sorted(tuple(a) for a in lam)     # lexicographic
+    brute = [a for a in itertools.product(range(6), repeat=3) if max(wk * ak for wk, ak in zip(w, a)) <= q]
+    assert sorted(tuple(a) for a in lam) == sorted(brute)
+
+
+def test_total_degree_set_is_inside_tensor_set_and_equal_in_one_dimension():
+    for w, q in [([1.0, 1.0, 1.0], 3.0), ([1.0, 2.0, 4.0, 8.0], 4.0), ([0.5, 1.5], 2.0)]:
+        td = {tuple(a) for a in o.index_set(w, q)}
+        tp = {tuple(a) for a in o.index_set(w, q, "tensor")}
+        assert td <= tp and (len(w) == 1 or td != tp)
+    np.testing.assert_array_equal(o.index_set([1.0], 6.0), o.index_set([1.0], 6.0, "tensor"))
+
+
+def test_tensor_expansion_reproduces_a_mixed_degree_monomial():
+    """x1^q x2^q lies in the tensor-product space but not in the total-degree
+    space of degree q: the tensor expansion interpolates it exactly, the
+    total-degree one does not."""
+    q = 3
+    f = lambda X: X[:, 0] ** q * X[:, 1] ** q
+    rng = np.random.default_rng(11)
+    T = rng.random((40, 2))
+    errs = {}
+    for shape in ("tensor", "total"):
+        ex = o.make_expansion(np.ones(2), float(q), shape=shape)
+        coef = np.linalg.solve(ex.V, f(ex.nodes))
+        errs[shape] = np.max(np.abs(o.basis_eval(ex.Lam, T) @ coef - f(T)))
+    assert errs["tensor"] <= 1e-12
+    assert errs["total"] > 1e-4
