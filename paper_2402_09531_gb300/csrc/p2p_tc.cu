@@ -38,11 +38,10 @@ constexpr int kCompWarps = 8;
 constexpr int kTcThreads = (kCompWarps + 2) * 32;   // compute warps, MMA warp, TMA warp
 constexpr int kChunkS = 32;                          // sources per A buffer
 constexpr int kTmemCols = 256;
-// Sleeps of the MMA and TMA threads between polls: a longer first sleep
-// (about half of a chunk's, or of a block's, evaluation time), then short
-// steps, so that the control threads take few issue slots from the compute
-// warps on their sub-partitions.
-constexpr uint32_t kMmaFirstNs = 384, kMmaStepNs = 96;
+// Sleeps of the control threads between polls.  The MMA thread polls
+// briskly (the compute warps wait for its commits two chunks later); the TMA
+// thread sleeps longer first (about half a block's evaluation time).
+constexpr uint32_t kMmaFirstNs = 64, kMmaStepNs = 64;
 constexpr uint32_t kTmaFirstNs = 2000, kTmaStepNs = 250;
 constexpr int kRow = 256;                // shared-memory row stride (floats) of the coordinates
 
