@@ -187,8 +187,15 @@ dwfmm_status dwfmm_solve(dwfmm_plan plan, double lambda, const double* f, double
  * (R int32: 0 running, 1 converged, 2 breakdown), iters (R int32) and rr (R
  * doubles, ||r||^2) describe that point (any may be NULL).
  * dwfmm_cg_result copies the current c (host or device, ld >= N; a host
- * copy synchronises `stream`).  Errors: STATE (no tree / no cg_begin),
- * INVALID_ARG (f not a device buffer, nrhs outside 1..max_rhs), CUDA. */
+ * copy synchronises `stream`).  On a stream other than the legacy default
+ * stream and with the phase timers off, dwfmm_cg_step captures its
+ * iterations into a CUDA graph the second time it is called with the same
+ * tree, R, lambda, iteration count and stream, and replays that graph from
+ * then on (small problems are bound by the host's kernel-launch rate); the
+ * first call with a new combination launches plainly, and so does every
+ * call if a capture ever fails.  The results are identical either way.
+ * Errors: STATE (no tree / no cg_begin), INVALID_ARG (f not a device buffer,
+ * nrhs outside 1..max_rhs), CUDA. */
 dwfmm_status dwfmm_cg_begin(dwfmm_plan plan, double lambda, const double* f, int32_t nrhs, int64_t ld,
                             double rtol, void* stream);
 dwfmm_status dwfmm_cg_step(dwfmm_plan plan, int32_t iters, void* stream);

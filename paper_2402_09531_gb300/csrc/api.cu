@@ -98,6 +98,7 @@ void Plan::free_all() {
   if (ev_join) cudaEventDestroy(ev_join);
   if (ev_scaled) cudaEventDestroy(ev_scaled);
   ev_scaled = nullptr;
+  cgs.drop_graph();
   cgs.d_int.release();
   if (cgs.h_snap) cudaFreeHost(cgs.h_snap);
   cgs.h_snap = nullptr;
@@ -249,6 +250,8 @@ dwfmm_status dwfmm_tree_build(dwfmm_plan plan, const double* pts, int64_t n, int
     if (n > 0 && (!pts || ld < P.d)) dw::fail(DWFMM_ERR_INVALID_ARG, "pts is NULL or ld < d");
     bind_stream(P, stream);
     P.free_tree();
+    P.cgs.drop_graph();
+    ++P.tree_gen;
     const double* dev = pts;
     dw::DBuf<double> staged;
     if (n > 0 && !is_device_pointer(pts)) {

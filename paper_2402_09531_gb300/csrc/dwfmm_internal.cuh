@@ -169,6 +169,25 @@ struct Timers {
 };
 
 // Incremental CG state (device scalars; pinned status snapshot for polling).
+// What a captured CG-iteration graph depends on: replayed only while all of
+// it is unchanged (tree, right-hand sides, shift, iteration count,
+// precision, stream and the Krylov buffers).
+struct CgGraphKey {
+  int tree_gen = -1, R = 0, iters = 0;
+  double lam = 0.0;
+  bool fp64 = false;
+  cudaStream_t stream = nullptr;
+  const void* bufs[6] = {};
+  bool operator==(const CgGraphKey& o) const {
+    if (tree_gen != o.tree_gen || R != o.R || iters != o.iters || lam != o.lam || fp64 != o.fp64 ||
+        stream != o.stream)
+      return false;
+    for (int i = 0; i < 6; ++i)
+      if (bufs[i] != o.bufs[i]) return false;
+    return true;
+  }
+};
+
 struct CgState {
   int R = 0;
   double lam = 0.0, rtol = 1e-6;
@@ -176,12 +195,28 @@ struct CgState {
   DBuf<int> d_int;              // status[R], iters[R]
   int* h_snap = nullptr;        // pinned: status[R], iters[R] | rr[R] at byte 128*4
   cudaEvent_t ev = nullptr;
+  // CUDA graph of `iters` CG iterations (cg_step): the first step with a new
+  // key runs uncaptured (it sizes every buffer), the next captures, later
+  // steps replay.
+  CgGraphKey warm_key, graph_key;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool graphs_off = false;      // capture failed once: plain launches from then on
+  void drop_graph() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    exec = nullptr;
+    graph = nullptr;
+    graph_key = CgGraphKey{};
+    warm_key = CgGraphKey{};
+  }
 };
 
 struct Plan {
   // configuration
   int d = 0, kernel = 0, wrule = 0, leaf = 0, M = 0, prec = 0, max_rhs = 0;
   int iset = 0;   // dwfmm_index_set
+  int tree_gen = 0;   // incremented by every tree build
   double sigma = 1.0, q = 0.0, eta = 1.0;
   std::vector<double> gamma, w;
   cudaStream_t stream = nullptr;   // stream of the last call

@@ -262,15 +262,17 @@ namespace dw {
 namespace {
 
 // state layout (doubles): rr[R], pap[R], coef[R], bn2[R]; ints: status[R], iters[R]
+// rtol^2 goes to device memory, so that captured iterations read it there
+// (refinement rounds change the tolerance, not the graph).
 __global__ void k_cg_init(const double* rr, int R, double* st_rr, double* st_bn2, int* status, int* iters,
-                          double rtol) {
+                          double rtol, double* st_rtol2) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= R) return;
   st_rr[r] = rr[r];
   st_bn2[r] = rr[r];
   iters[r] = 0;
   status[r] = (rr[r] == 0.0) ? 1 : 0;   // 0 running, 1 converged, 2 breakdown
-  (void)rtol;
+  if (r == 0) *st_rtol2 = rtol * rtol;
 }
 
 __global__ void k_cg_alpha(const double* pap, const double* rr, int* status, double* alpha, int R) {
@@ -285,13 +287,13 @@ __global__ void k_cg_alpha(const double* pap, const double* rr, int* status, dou
 }
 
 __global__ void k_cg_beta(const double* rr_new, double* rr, const double* bn2, int* status, int* iters,
-                          double* beta, int R, double rtol2) {
+                          double* beta, int R, const double* rtol2) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= R) return;
   double b = 0.0;
   if (status[r] == 0) {
     iters[r] += 1;
-    if (rr_new[r] <= rtol2 * bn2[r]) status[r] = 1;
+    if (rr_new[r] <= *rtol2 * bn2[r]) status[r] = 1;
     b = rr_new[r] / rr[r];
     rr[r] = rr_new[r];
   }
@@ -335,11 +337,13 @@ void cg_begin(Plan& P, double lam, const double* f, int R, int64_t ld, double rt
   DW_CUDA(cudaMemcpyAsync(P.cg_r.p, P.cg_f.p, nr * sizeof(double), cudaMemcpyDeviceToDevice, P.stream));
   DW_CUDA(cudaMemcpyAsync(P.cg_p.p, P.cg_f.p, nr * sizeof(double), cudaMemcpyDeviceToDevice, P.stream));
   dots_dev(P, P.cg_r.p, P.cg_r.p, n, R, part, tmp);
-  k_cg_init<<<1, 64, 0, P.stream>>>(tmp, R, rr, bn2, S.d_int.p, S.d_int.p + R, rtol);
+  k_cg_init<<<1, 64, 0, P.stream>>>(tmp, R, rr, bn2, S.d_int.p, S.d_int.p + R, rtol, tmp + R);
   DW_CUDA(cudaGetLastError());
 }
 
-void cg_step(Plan& P, int iters) {
+// One CG iteration for every column on P.stream; nothing here waits for the
+// host, so a run of iterations can be captured into a CUDA graph.
+static void cg_iteration(Plan& P) {
   CgState& S = P.cgs;
   const int64_t n = P.N;
   const int R = S.R;
@@ -350,19 +354,94 @@ void cg_step(Plan& P, int iters) {
   double* coef = pap + R;
   double* bn2 = coef + R;
   double* tmp = bn2 + R;
+  double* rtol2 = tmp + R;
   int* status = S.d_int.p;
   int* its = S.d_int.p + R;
   const bool fp64 = P.prec == DWFMM_P_FP64;
-  for (int k = 0; k < iters; ++k) {
-    apply_op(P, P.cg_p.p, P.cg_ap.p, R, S.lam, fp64);
-    dots_dev(P, P.cg_p.p, P.cg_ap.p, n, R, part, pap);
-    k_cg_alpha<<<1, 64, 0, P.stream>>>(pap, rr, status, coef, R);
-    k_axpby<<<ceil_div(nr, 256), 256, 0, P.stream>>>(P.cg_p.p, P.cg_c.p, nullptr, coef, 1.0, nullptr, 0.0, n, n, R, 1.0);
-    k_axpby<<<ceil_div(nr, 256), 256, 0, P.stream>>>(P.cg_ap.p, P.cg_r.p, nullptr, coef, 1.0, nullptr, 0.0, n, n, R, -1.0);
-    dots_dev(P, P.cg_r.p, P.cg_r.p, n, R, part, tmp);
-    k_cg_beta<<<1, 64, 0, P.stream>>>(tmp, rr, bn2, status, its, coef, R, S.rtol * S.rtol);
-    k_axpby<<<ceil_div(nr, 256), 256, 0, P.stream>>>(P.cg_r.p, P.cg_p.p, nullptr, nullptr, 0.0, coef, 0.0, n, n, R, 1.0);
+  apply_op(P, P.cg_p.p, P.cg_ap.p, R, S.lam, fp64);
+  dots_dev(P, P.cg_p.p, P.cg_ap.p, n, R, part, pap);
+  k_cg_alpha<<<1, 64, 0, P.stream>>>(pap, rr, status, coef, R);
+  k_axpby<<<ceil_div(nr, 256), 256, 0, P.stream>>>(P.cg_p.p, P.cg_c.p, nullptr, coef, 1.0, nullptr, 0.0, n, n, R, 1.0);
+  k_axpby<<<ceil_div(nr, 256), 256, 0, P.stream>>>(P.cg_ap.p, P.cg_r.p, nullptr, coef, 1.0, nullptr, 0.0, n, n, R, -1.0);
+  dots_dev(P, P.cg_r.p, P.cg_r.p, n, R, part, tmp);
+  k_cg_beta<<<1, 64, 0, P.stream>>>(tmp, rr, bn2, status, its, coef, R, rtol2);
+  k_axpby<<<ceil_div(nr, 256), 256, 0, P.stream>>>(P.cg_r.p, P.cg_p.p, nullptr, nullptr, 0.0, coef, 0.0, n, n, R, 1.0);
+}
+
+// Run `iters` iterations from a captured graph when possible: the launch
+// sequence of an iteration is fixed for a tree, R, shift and buffer set, and
+// small problems are bound by the host's launch rate, not by the GPU.  The
+// first step with a new key runs plainly (it allocates whatever the matvec
+// allocates on first use), the second captures, later steps replay.  Returns
+// false when the caller should launch plainly (legacy default stream, phase
+// timers on, first step of a key, or a capture that failed once).
+static bool cg_step_graph(Plan& P, int iters) {
+  CgState& S = P.cgs;
+  if (iters <= 0 || P.stream == nullptr || P.tm.on || S.graphs_off) return false;
+  CgGraphKey key;
+  key.tree_gen = P.tree_gen;
+  key.R = S.R;
+  key.iters = iters;
+  key.lam = S.lam;
+  key.fp64 = P.prec == DWFMM_P_FP64;
+  key.stream = P.stream;
+  const void* bufs[6] = {P.cg_p.p, P.cg_ap.p, P.cg_c.p, P.cg_r.p, P.cg_dot.p, S.d_int.p};
+  for (int i = 0; i < 6; ++i) key.bufs[i] = bufs[i];
+  if (S.exec && S.graph_key == key) {
+    DW_CUDA(cudaGraphLaunch(S.exec, P.stream));
+    return true;
   }
+  if (!(S.warm_key == key)) {
+    S.warm_key = key;
+    return false;
+  }
+  if (S.exec) cudaGraphExecDestroy(S.exec);
+  if (S.graph) cudaGraphDestroy(S.graph);
+  S.exec = nullptr;
+  S.graph = nullptr;
+  if (cudaStreamBeginCapture(P.stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    (void)cudaGetLastError();
+    S.graphs_off = true;
+    return false;
+  }
+  try {
+    for (int k = 0; k < iters; ++k) cg_iteration(P);
+  } catch (...) {
+    // a call in the path refused capture: nothing ran; launch plainly from now on
+    cudaGraph_t g = nullptr;
+    (void)cudaStreamEndCapture(P.stream, &g);
+    if (g) cudaGraphDestroy(g);
+    (void)cudaGetLastError();
+    S.graphs_off = true;
+    return false;
+  }
+  cudaGraph_t g = nullptr;
+  if (cudaStreamEndCapture(P.stream, &g) != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    (void)cudaGetLastError();
+    S.graphs_off = true;
+    return false;   // nothing was enqueued: the caller launches plainly
+  }
+  cudaGraphExec_t e = nullptr;
+  if (cudaGraphInstantiate(&e, g, 0) != cudaSuccess) {
+    cudaGraphDestroy(g);
+    (void)cudaGetLastError();
+    S.graphs_off = true;
+    return false;
+  }
+  S.graph = g;
+  S.exec = e;
+  S.graph_key = key;
+  DW_CUDA(cudaGraphLaunch(S.exec, P.stream));
+  return true;
+}
+
+void cg_step(Plan& P, int iters) {
+  CgState& S = P.cgs;
+  const int R = S.R;
+  double* rr = P.cg_dot.p + kDotBlocks * R;
+  if (!cg_step_graph(P, iters))
+    for (int k = 0; k < iters; ++k) cg_iteration(P);
   // status snapshot for the non-blocking poll
   DW_CUDA(cudaMemcpyAsync(S.h_snap, S.d_int.p, 2 * R * sizeof(int), cudaMemcpyDeviceToHost, P.stream));
   DW_CUDA(cudaMemcpyAsync(reinterpret_cast<char*>(S.h_snap) + 128 * sizeof(int), rr, R * sizeof(double),

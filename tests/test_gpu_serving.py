@@ -101,3 +101,62 @@ def test_incremental_cg_matches_blocking_solve():
     torch.cuda.synchronize()
     assert int(iters.max()) == its
     np.testing.assert_allclose(cb.cpu().numpy(), ca.cpu().numpy(), rtol=0, atol=1e-12 * float(ca.abs().max()))
+
+
+def _run_incremental(plan, lam, fd, steps, stream, rtol=1e-10, rounds=400):
+    """Incremental CG on `stream` with the given iteration counts per step
+    (cycled); returns (status, iters, c)."""
+    import torch
+    with torch.cuda.stream(stream):
+        plan.cg_begin(lam, fd, rtol=rtol, stream=stream)
+        for k in range(rounds):
+            plan.cg_step(steps[k % len(steps)], stream=stream)
+            stream.synchronize()
+            ready, status, iters, rr = plan.cg_poll()
+            assert ready
+            if np.all(status != 0):
+                break
+        c = torch.zeros_like(fd)
+        plan.cg_result(c, stream=stream)
+        stream.synchronize()
+    return status, iters, c.cpu().numpy()
+
+
+@pytest.mark.parametrize("precision,nrhs,rtol", [("fp64", 2, 1e-10), ("mixed", 16, 1e-5)])
+def test_captured_cg_iterations_equal_plain_launches(precision, nrhs, rtol):
+    """cg_step replays a captured CUDA graph of its iterations from the second
+    step with the same configuration on a non-default stream.  Constant step
+    sizes take that path; alternating step sizes never do (every step starts a
+    new configuration).  Both must give the same solution bit for bit, also
+    after the tree is rebuilt on other sites (the graph must not be reused)."""
+    import torch
+    from paper_2402_09531_gb300 import Plan
+    w = di.scaled(di.mixed_gauss_d10(), 3000, nrhs=nrhs)
+    X, f = di.sites_and_rhs(w)
+    X2 = X[::-1].copy() * 0.9
+    kw = dict(d=w.d, kernel=w.kernel, gamma=w.gamma, q=4.0, eta=1.0, leaf_size=64, precision=precision,
+              max_rhs=nrhs)
+    s = torch.cuda.Stream()
+    fd = torch.from_numpy(f).cuda()
+    torch.cuda.synchronize()
+    results = []
+    for steps in ([5], [4, 6]):
+        p = Plan(**kw)
+        out = []
+        for pts in (X, X2):
+            with torch.cuda.stream(s):
+                p.tree_build(torch.from_numpy(pts).cuda(), stream=s)
+            st, its, c = _run_incremental(p, 2.0, fd, steps, s, rtol=rtol)
+            assert np.all(st == 1)
+            out.append(c)
+        results.append(out)
+        p.close()
+    for a, b in zip(*results):
+        assert np.array_equal(a, b)
+    # and a fresh plan on the second tree agrees with the rebuilt one
+    q = Plan(**kw)
+    with torch.cuda.stream(s):
+        q.tree_build(torch.from_numpy(X2).cuda(), stream=s)
+    _, _, c2 = _run_incremental(q, 2.0, fd, [5], s, rtol=rtol)
+    assert np.array_equal(c2, results[0][1])
+    q.close()
