@@ -16,6 +16,7 @@ runs on one GPU; replicas scale weakly); rank 0 prints.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import math
 import os
@@ -388,6 +389,51 @@ def _serve(reqs, precision, lam):
     return out
 
 
+def _serve_poisson(reqs, precision, lam, loads=(0.5, 0.8, 1.0), seed=7):
+    """Offered-load sweep: the closed-loop rate (all requests at t=0) sets the
+    scale; then Poisson arrivals at each fraction of it (seeded exponential
+    gaps), p50/p99 latency measured from each request's arrival."""
+    import numpy as np
+    from paper_2402_09531_gb300.serving import Request, Server, summarize
+    base = _serve(reqs, precision, lam)
+    rate = base["solves_per_s"]
+    rng = np.random.default_rng(seed)
+    out = {"closed_loop_solves_per_s": rate, "requests": len(reqs)}
+    for load in loads:
+        gaps = rng.exponential(1.0 / (load * rate), size=len(reqs))
+        arrival = np.cumsum(gaps) - gaps[0]
+        rs = [Request(rid=r.rid, X=r.X, f=r.f, kernel=r.kernel, gamma=r.gamma, q=r.q, eta=r.eta, leaf=r.leaf,
+                      weight_rule=r.weight_rule, lam=lam, rtol=r.rtol, maxit=r.maxit, arrival=float(a))
+              for r, a in zip(reqs, arrival)]
+        srv = Server(precision=precision, max_active=8)
+        srv.run([dataclasses.replace(rs[0], rid=-1, arrival=0.0)])   # warm-up (plan pool)
+        t0 = time.perf_counter()
+        res = srv.run(rs)
+        summ = summarize(res, time.perf_counter() - t0)
+        out[f"load_{load:g}"] = {"offered_per_s": load * rate, **{k: summ[k] for k in
+                                 ("ok", "p50_ms", "p99_ms", "solves_per_s", "mean_iters")},
+                                 "peak_active": srv.peak_active}
+        srv.close()
+    return out
+
+
+def _sample_requests(count, nmax):
+    """The first `count` requests of the serving stream with N <= nmax (eta=2,
+    Sec. 6.2 weights: the readings for the stream's unstated parameters)."""
+    import dwfmm_inputs as di
+    from paper_2402_09531_gb300.serving import Request
+    reqs = []
+    for w in di.serving_requests(2000):
+        if w.n > nmax:
+            continue
+        X, f = di.sites_and_rhs(w, nrhs=1)
+        reqs.append(Request(rid=len(reqs), X=X, f=f, kernel=w.kernel, gamma=w.gamma, q=w.q, eta=2.0,
+                            leaf=w.leaf, weight_rule="paper_logrho", lam=w.lam, rtol=w.rtol, maxit=4000))
+        if len(reqs) >= count:
+            break
+    return reqs
+
+
 def run_solve_sample(args):
     """CG solve latency on a bounded sample of the serving request stream
     (d=16, gamma_k=2^-k, exponential kernel, q=6, rtol=1e-6; eta=2 and the
@@ -395,24 +441,20 @@ def run_solve_sample(args):
     by the continuous-batching server.  lambda=1e-6 needs the float64
     operator (the float32 operator's rounding exceeds lambda by orders of
     magnitude and refinement diverges); float32 + float64-residual
-    refinement is compared with float64 at lambda=1e-2."""
-    import dwfmm_inputs as di
-    from paper_2402_09531_gb300.serving import Request
-    reqs = []
-    for w in di.serving_requests(2000):
-        if w.n > args.solve_nmax:
-            continue
-        X, f = di.sites_and_rhs(w, nrhs=1)
-        reqs.append(Request(rid=len(reqs), X=X, f=f, kernel=w.kernel, gamma=w.gamma, q=w.q, eta=2.0,
-                            leaf=w.leaf, weight_rule="paper_logrho", lam=w.lam, rtol=w.rtol, maxit=4000))
-        if len(reqs) >= args.solve_requests:
-            break
+    refinement is compared with float64 at lambda=1e-2.  A Poisson
+    offered-load sweep (0.5, 0.8, 1.0 of the closed-loop rate) runs the mixed
+    server on a larger sample."""
+    reqs = _sample_requests(args.solve_requests, args.solve_nmax)
+    sweep = _sample_requests(args.sweep_requests, args.sweep_nmax)
     return {"workload": "serving stream sample: d=16, gamma_k=2^-k, exp kernel, q=6, eta=2, Sec. 6.2 weights, "
                         "leaf 128, rtol=1e-6, all arriving at t=0, 8 active slots",
             "n_range": [min(r.X.shape[0] for r in reqs), max(r.X.shape[0] for r in reqs)],
             "fp64_lambda_1e-6": _serve(reqs, "fp64", 1e-6),
             "fp64_lambda_1e-2": _serve(reqs, "fp64", 1e-2),
-            "mixed_lambda_1e-2": _serve(reqs, "mixed", 1e-2)}
+            "mixed_lambda_1e-2": _serve(reqs, "mixed", 1e-2),
+            "mixed_lambda_1e-2_poisson": {"n_range": [min(r.X.shape[0] for r in sweep),
+                                                      max(r.X.shape[0] for r in sweep)],
+                                          **_serve_poisson(sweep, "mixed", 1e-2)}}
 
 
 def run_reference(args):
@@ -453,6 +495,8 @@ def main():
                     help="also time one float64 matvec of the same workload (about a minute at N=2^20)")
     ap.add_argument("--solve-requests", type=int, default=8)
     ap.add_argument("--solve-nmax", type=int, default=3000)
+    ap.add_argument("--sweep-requests", type=int, default=32)
+    ap.add_argument("--sweep-nmax", type=int, default=3000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--oracle-sample", default=None)
     args = ap.parse_args()
