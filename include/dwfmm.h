@@ -210,6 +210,28 @@ dwfmm_status dwfmm_cg_result(dwfmm_plan plan, double* c, int64_t ld, void* strea
 dwfmm_status dwfmm_residual(dwfmm_plan plan, double lambda, const double* f, const double* c, double* r,
                             int32_t nrhs, int64_t ld, double* relres, void* stream);
 
+/* One step of iterative refinement with a minimal-residual step length (the
+ * paper runs plain CG; this is the solver's own safeguard for reduced-
+ * precision plans).  On entry r holds the float64 residual
+ * f - (K_tilde + lambda I) c and delta a correction, typically an inner CG
+ * solve of the plan's reduced-precision system with right-hand side r.  Per
+ * column, a* = (r, A delta) / (A delta, A delta) with the float64 operator A
+ * minimises ||r - a A delta||; the step is alpha = 1 (plain refinement)
+ * when a* > 1/2, where that lowers the residual, else alpha = a* (0 when
+ * A delta = 0 or a* is not finite).  Then c += alpha delta and
+ * r -= alpha A delta, so the float64 residual never grows, also when the
+ * float32 operator's error approaches lambda and the inner solve returns a
+ * poor correction (plain refinement, c += delta, then diverges).  f, c, delta, r: host or device,
+ * column-major N x nrhs, leading dimension ld >= N; c and r are updated in
+ * place.  alpha and relres (host, nrhs doubles each, may be NULL) receive the
+ * step lengths and ||r|| / ||f|| after the step.  Synchronises `stream`.
+ * dwfmm_residual and dwfmm_refine use the incremental CG's scratch: call them
+ * between solves (after dwfmm_cg_result, before the next dwfmm_cg_begin), not
+ * between dwfmm_cg_step calls of one solve.  Errors: STATE (no tree),
+ * INVALID_ARG (NULL buffer, ld < N, nrhs outside 1..max_rhs), CUDA. */
+dwfmm_status dwfmm_refine(dwfmm_plan plan, double lambda, const double* f, double* c, const double* delta,
+                          double* r, int32_t nrhs, int64_t ld, double* alpha, double* relres, void* stream);
+
 /* The kernel interpolant at new points (Sec. 2: s_X(x) = sum_j alpha_j
  * K(x_j, x); Sec. 6.2 measures its prediction error at test points):
  * out(t, r) = sum_j phi(||x_t - x_j|| / sigma) c(j, r) for t < nt, evaluated

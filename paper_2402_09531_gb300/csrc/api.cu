@@ -549,6 +549,49 @@ dwfmm_status dwfmm_residual(dwfmm_plan plan, double lambda, const double* f, con
   });
 }
 
+dwfmm_status dwfmm_refine(dwfmm_plan plan, double lambda, const double* f, double* c, const double* delta,
+                          double* r, int32_t nrhs, int64_t ld, double* alpha, double* relres, void* stream) {
+  if (!plan) return DWFMM_ERR_INVALID_ARG;
+  Plan& P = plan->P;
+  return guarded(&P, [&]() -> dwfmm_status {
+    if (!P.have_tree) dw::fail(DWFMM_ERR_STATE, "refine before tree_build");
+    if (nrhs < 1 || nrhs > P.max_rhs) dw::fail(DWFMM_ERR_INVALID_ARG, "nrhs outside 1..max_rhs");
+    if (P.N == 0) return DWFMM_OK;
+    if (!f || !c || !delta || !r || ld < P.N) dw::fail(DWFMM_ERR_INVALID_ARG, "NULL buffer or ld < N");
+    bind_stream(P, stream);
+    const int64_t n = P.N;
+    const size_t nr = static_cast<size_t>(n) * nrhs;
+    dw::DBuf<double> cd, dd, rd, fd;
+    cd.alloc(nr);
+    dd.alloc(nr);
+    rd.alloc(nr);
+    fd.alloc(nr);
+    auto in = [&](double* dst, const double* src) {
+      DW_CUDA(cudaMemcpy2DAsync(dst, n * sizeof(double), src, ld * sizeof(double), n * sizeof(double), nrhs,
+                                cudaMemcpyDefault, P.stream));
+    };
+    in(cd.p, c);
+    in(dd.p, delta);
+    in(rd.p, r);
+    in(fd.p, f);
+    std::vector<double> al(nrhs), rel(nrhs);
+    dw::refine64(P, lambda, fd.p, cd.p, dd.p, rd.p, nrhs, al.data(), rel.data());
+    auto out = [&](double* dst, const double* src) {
+      DW_CUDA(cudaMemcpy2DAsync(dst, ld * sizeof(double), src, n * sizeof(double), n * sizeof(double), nrhs,
+                                cudaMemcpyDefault, P.stream));
+    };
+    out(c, cd.p);
+    out(r, rd.p);
+    DW_CUDA(cudaStreamSynchronize(P.stream));
+    dw::check_device_error(P);
+    for (int k = 0; k < nrhs; ++k) {
+      if (alpha) alpha[k] = al[k];
+      if (relres) relres[k] = rel[k];
+    }
+    return DWFMM_OK;
+  });
+}
+
 dwfmm_status dwfmm_evaluate(dwfmm_plan plan, const double* targets, int64_t nt, int64_t ld_t, const double* c,
                             int64_t ld_c, double* out, int64_t ld_o, int32_t nrhs, void* stream) {
   if (!plan) return DWFMM_ERR_INVALID_ARG;

@@ -357,6 +357,10 @@ void cg_step(Plan& P, int iters);
 bool cg_poll(Plan& P, int* status, int* iters, double* rr);
 void cg_result(Plan& P, double* c, int64_t ld);
 void residual64(Plan& P, double lam, const double* f, const double* c, double* r, int R, double* relres);
+void refine_step(Plan& P, double lam, double* c, const double* delta, double* r, int R, double* w,
+                 double* part, double* dev3);
+void refine64(Plan& P, double lam, const double* f, double* c, const double* delta, double* r, int R,
+              double* alpha, double* relres);
 
 inline int ceil_div(int64_t a, int64_t b) { return static_cast<int>((a + b - 1) / b); }
 inline int round_up(int v, int m) { return (v + m - 1) / m * m; }

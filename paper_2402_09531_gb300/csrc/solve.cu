@@ -147,6 +147,11 @@ int cg(Plan& P, Vecs& V, const double* b, double* x, int R, double lam, double r
 
 }  // namespace
 
+// One refinement step with a minimal-residual length (defined with the
+// device-side CG helpers below): c += alpha delta, r -= alpha (A64 delta).
+void refine_step(Plan& P, double lam, double* c, const double* delta, double* r, int R, double* w,
+                 double* part, double* dev3);
+
 dwfmm_status solve(Plan& P, double lam, const double* f, double* c, int R, int64_t ld, double rtol,
                    int maxit, int* iters, double* relres) {
   const int64_t n = P.N;
@@ -163,7 +168,7 @@ dwfmm_status solve(Plan& P, double lam, const double* f, double* c, int R, int64
   P.cg_c.alloc(nr);
   P.cg_f.alloc(nr);
   P.cg_tmp.alloc(nr);
-  P.cg_dot.alloc(static_cast<size_t>(kDotBlocks) * R + 2 * R + 2);
+  P.cg_dot.alloc(static_cast<size_t>(kDotBlocks) * R + 8 * R + 8);
   Vecs V{P.cg_c.p, P.cg_r.p, P.cg_p.p, P.cg_ap.p, P.cg_dot.p, P.cg_dot.p + kDotBlocks * R,
          P.cg_dot.p + kDotBlocks * R + R};
   // compact copy of f (leading dimension n)
@@ -182,7 +187,10 @@ dwfmm_status solve(Plan& P, double lam, const double* f, double* c, int R, int64
       else if (st[r] == 2 && status == DWFMM_OK) status = DWFMM_ERR_NOT_CONVERGED;
     }
   } else {
-    // iterative refinement: c += CG32(f - A64 c)
+    // iterative refinement: delta = CG32(r), c += alpha delta, r -= alpha A64 delta
+    // with alpha = 1 where that lowers the float64 residual, else the
+    // minimal-residual length (when the float32 operator's error approaches
+    // lambda a capped inner CG can return a correction that would raise it)
     DW_CUDA(cudaMemsetAsync(V.c, 0, nr * sizeof(double), P.stream));
     DBuf<double> delta, rhs;
     delta.alloc(nr);
@@ -215,14 +223,19 @@ dwfmm_status solve(Plan& P, double lam, const double* f, double* c, int R, int64
       total_it += it;
       bool broke = false;
       for (int r = 0; r < R; ++r) broke |= st[r] == 1;
-      k_axpby<<<ceil_div(nr, 256), 256, 0, P.stream>>>(delta.p, V.c, nullptr, nullptr, 1.0, nullptr, 0.0, n, n, R, 1.0);
-      // rhs = f - (K64 c + lam c)
-      apply_op(P, V.c, P.cg_tmp.p, R, lam, true);
-      DW_CUDA(cudaMemcpyAsync(rhs.p, P.cg_f.p, nr * sizeof(double), cudaMemcpyDeviceToDevice, P.stream));
-      k_axpby<<<ceil_div(nr, 256), 256, 0, P.stream>>>(P.cg_tmp.p, rhs.p, nullptr, nullptr, 1.0, nullptr, 0.0, n, n, R, -1.0);
+      double* dev3 = P.cg_dot.p + kDotBlocks * R + 2 * R;
+      refine_step(P, lam, V.c, delta.p, rhs.p, R, P.cg_tmp.p, V.part, dev3);
       if (broke) {
-        status = DWFMM_ERR_BREAKDOWN;
-        break;
+        // a breakdown of the inner CG is fatal only if its correction did not help
+        std::vector<double> alpha(R);
+        DW_CUDA(cudaMemcpyAsync(alpha.data(), dev3 + 2 * R, R * sizeof(double), cudaMemcpyDeviceToHost, P.stream));
+        DW_CUDA(cudaStreamSynchronize(P.stream));
+        bool moved = false;
+        for (int r = 0; r < R; ++r) moved |= alpha[r] != 0.0;
+        if (!moved) {
+          status = DWFMM_ERR_BREAKDOWN;
+          break;
+        }
       }
     }
     if (status == DWFMM_ERR_NOT_CONVERGED) {
@@ -306,7 +319,36 @@ void dots_dev(Plan& P, const double* a, const double* b, int64_t n, int R, doubl
   k_dot_final<<<ceil_div(R, 64), 64, 0, P.stream>>>(part, kDotBlocks, R, out);
 }
 
+// Step length per column from a* = (r, w) / (w, w): the plain refinement
+// step 1 whenever it lowers ||r - alpha w|| (a* > 1/2), else a*; 0 when
+// w = 0 or a* is not finite.  Either way ||r - alpha w|| <= ||r||.
+__global__ void k_minres_alpha(const double* num, const double* den, double* alpha, int R) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= R) return;
+  double a = den[r] > 0.0 ? num[r] / den[r] : 0.0;
+  if (!isfinite(a)) a = 0.0;
+  alpha[r] = a > 0.5 ? 1.0 : a;
+}
+
 }  // namespace
+
+// c += alpha delta and r -= alpha w with w = (K64 + lam I) delta and alpha
+// per column from k_minres_alpha (never raising ||r||); r must hold f - (K64 + lam I) c on
+// entry and holds the same for the new c on return.  All buffers compact
+// (leading dimension N); w: N x R scratch; part: dot partials; dev3: 3R
+// doubles (numerators, denominators, alpha).  No host synchronisation.
+void refine_step(Plan& P, double lam, double* c, const double* delta, double* r, int R, double* w,
+                 double* part, double* dev3) {
+  const int64_t n = P.N;
+  const int64_t nr = n * R;
+  apply_op(P, delta, w, R, lam, true);
+  dots_dev(P, r, w, n, R, part, dev3);
+  dots_dev(P, w, w, n, R, part, dev3 + R);
+  k_minres_alpha<<<ceil_div(R, 64), 64, 0, P.stream>>>(dev3, dev3 + R, dev3 + 2 * R, R);
+  k_axpby<<<ceil_div(nr, 256), 256, 0, P.stream>>>(delta, c, nullptr, dev3 + 2 * R, 1.0, nullptr, 0.0, n, n, R, 1.0);
+  k_axpby<<<ceil_div(nr, 256), 256, 0, P.stream>>>(w, r, nullptr, dev3 + 2 * R, 1.0, nullptr, 0.0, n, n, R, -1.0);
+  DW_CUDA(cudaGetLastError());
+}
 
 void cg_begin(Plan& P, double lam, const double* f, int R, int64_t ld, double rtol) {
   const int64_t n = P.N;
@@ -489,6 +531,25 @@ void residual64(Plan& P, double lam, const double* f, const double* c, double* r
   std::vector<double> rn(R), fn(R);
   double* part = P.cg_dot.p;
   double* out = part + kDotBlocks * R;
+  dots(P, r, r, n, n, R, part, out, rn.data());
+  dots(P, f, f, n, n, R, part, out, fn.data());
+  for (int k = 0; k < R; ++k) relres[k] = fn[k] > 0.0 ? std::sqrt(rn[k] / fn[k]) : 0.0;
+}
+
+// refine_step on compact device buffers, then alpha and ||r|| / ||f|| per
+// column to the host.  Synchronises the plan's stream.
+void refine64(Plan& P, double lam, const double* f, double* c, const double* delta, double* r, int R,
+              double* alpha, double* relres) {
+  const int64_t n = P.N;
+  const int64_t nr = n * R;
+  P.cg_tmp.alloc(nr);
+  P.cg_dot.alloc(static_cast<size_t>(kDotBlocks) * R + 8 * R + 8);
+  double* part = P.cg_dot.p;
+  double* dev3 = part + static_cast<size_t>(kDotBlocks) * R + 2 * R;
+  refine_step(P, lam, c, delta, r, R, P.cg_tmp.p, part, dev3);
+  DW_CUDA(cudaMemcpyAsync(alpha, dev3 + 2 * R, R * sizeof(double), cudaMemcpyDeviceToHost, P.stream));
+  std::vector<double> rn(R), fn(R);
+  double* out = part + static_cast<size_t>(kDotBlocks) * R;
   dots(P, r, r, n, n, R, part, out, rn.data());
   dots(P, f, f, n, n, R, part, out, fn.data());
   for (int k = 0; k < R; ++k) relres[k] = fn[k] > 0.0 ? std::sqrt(rn[k] / fn[k]) : 0.0;

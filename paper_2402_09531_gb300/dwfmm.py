@@ -35,6 +35,7 @@ EXPORTS = ("dwfmm_plan_create", "dwfmm_plan_set_nodes", "dwfmm_tree_build", "dwf
            "dwfmm_plan_info", "dwfmm_plan_export", "dwfmm_tree_export", "dwfmm_lists_export",
            "dwfmm_set_profiling", "dwfmm_phase_times", "dwfmm_direct_sum_noalloc",
            "dwfmm_cg_begin", "dwfmm_cg_step", "dwfmm_cg_poll", "dwfmm_cg_result", "dwfmm_residual",
+           "dwfmm_refine",
            "dwfmm_batch_create", "dwfmm_batch_matvec", "dwfmm_batch_info", "dwfmm_batch_destroy",
            "dwfmm_evaluate")
 
@@ -81,6 +82,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "dwfmm_cg_poll": (i32, [P, C.POINTER(i32), P, P, P]),
         "dwfmm_cg_result": (i32, [P, P, i64, P]),
         "dwfmm_residual": (i32, [P, dbl, P, P, P, i32, i64, P, P]),
+        "dwfmm_refine": (i32, [P, dbl, P, P, P, P, i32, i64, P, P, P]),
         "dwfmm_batch_create": (i32, [P, P, i32, P, C.POINTER(P)]),
         "dwfmm_batch_matvec": (i32, [P, P, P, P]),
         "dwfmm_batch_info": (i32, [P, C.POINTER(i32), P, C.POINTER(i64)]),
@@ -245,6 +247,19 @@ class Plan:
         self.check(self._l.dwfmm_residual(self.h, float(lam), _ptr(f), _ptr(c), _ptr(r), R, ld,
                                           rel.ctypes.data, _stream_handle(stream)))
         return rel
+
+    def refine(self, lam: float, f, c, delta, r, stream=None):
+        """c += alpha delta, r -= alpha (K64 + lam I) delta with a per-column
+        alpha that never raises ||r|| (1 where plain refinement lowers it,
+        else the minimal-residual length); r must hold f - (K64 + lam I) c.
+        c and r are updated in place.  Returns (alpha, relres)."""
+        R = int(f.shape[0])
+        ld = int(f.stride(0)) if hasattr(f, "stride") and callable(f.stride) else int(f.strides[0] // 8)
+        alpha = np.zeros(R)
+        rel = np.zeros(R)
+        self.check(self._l.dwfmm_refine(self.h, float(lam), _ptr(f), _ptr(c), _ptr(delta), _ptr(r), R, ld,
+                                        alpha.ctypes.data, rel.ctypes.data, _stream_handle(stream)))
+        return alpha, rel
 
     def info(self):
         nx, nf, nn, dep = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int32()

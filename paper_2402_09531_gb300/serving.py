@@ -7,9 +7,10 @@ node setup of Sec. 5.4 runs once per configuration), a CUDA stream and its
 Krylov state on the device.  Each pass of the loop enqueues a few CG
 iterations (dwfmm_cg_step: no host synchronisation) for every request whose
 previous batch has finished (dwfmm_cg_poll: never blocks), so the matvecs of
-all active requests overlap on the GPU.  A finished inner solve of a float32
-plan is refined with the float64 operator (dwfmm_residual) until the
-float64 relative residual meets the request's tolerance.  Finished requests
+all active requests overlap on the GPU.  A finished inner solve is folded
+into the solution with a minimal-residual step against the float64
+operator (dwfmm_refine), and float32/mixed plans restart the inner CG on
+the float64 residual until it meets the request's tolerance.  Finished requests
 release their slot, memory and plan.
 
 This module only schedules; every numerical step runs in libdwfmm.so.
@@ -81,6 +82,7 @@ class _Active:
     fd: object               # device rhs of the current inner solve
     f0: object               # device original rhs
     acc: object              # device accumulated solution
+    r: object                # device float64 residual f0 - (K64 + lam I) acc
     t_admit: float
     nbytes: int
     iters: int = 0
@@ -142,11 +144,12 @@ class Server:
             Xd = torch.from_numpy(r.X).to(self.dev, non_blocking=False)
             f0 = torch.from_numpy(np.ascontiguousarray(r.f)).to(self.dev)
             acc = torch.zeros_like(f0)
+            res = f0.clone()   # the residual of acc = 0
         plan.tree_build(Xd, stream=stream)
         plan.cg_begin(r.lam, f0, rtol=self._inner_tol(r.rtol, 1.0), stream=stream)
         plan.cg_step(self.step_iters, stream=stream)
         self.used += nbytes
-        return _Active(r, plan, stream, key, f0, f0, acc, t_now, nbytes)
+        return _Active(r, plan, stream, key, f0, f0, acc, res, t_now, nbytes)
 
     def _finish(self, a: _Active, status: str, relres, t_now: float) -> Result:
         torch = self.torch
@@ -178,26 +181,24 @@ class Server:
         if running and total < a.req.maxit and a_iters < inner_cap:
             a.plan.cg_step(self.step_iters, stream=a.stream)
             return None
-        # inner solve finished: fold it into the accumulated solution
+        # inner solve finished: fold its correction in (dwfmm_refine: the plain
+        # step where it lowers the float64 residual, else the minimal-residual
+        # one, so a poor inner solve cannot raise it)
         with torch.cuda.stream(a.stream):
-            tmp = torch.empty_like(a.acc)
-        a.plan.cg_result(tmp, stream=a.stream)
-        with torch.cuda.stream(a.stream):
-            a.acc += tmp
+            delta = torch.empty_like(a.acc)
+        a.plan.cg_result(delta, stream=a.stream)
         a.iters = total
-        if np.any(st == 2):
-            return self._finish(a, "breakdown", [float("nan")] * len(st), t_now)
-        with torch.cuda.stream(a.stream):
-            r = torch.empty_like(a.acc)
-        rel = a.plan.residual(a.req.lam, a.f0, a.acc, r=r, stream=a.stream)
+        alpha, rel = a.plan.refine(a.req.lam, a.f0, a.acc, delta, a.r, stream=a.stream)
         if np.all(rel <= a.req.rtol):
             return self._finish(a, "ok", rel, t_now)
+        if np.any(st == 2) and np.all(alpha == 0.0):
+            return self._finish(a, "breakdown", rel, t_now)
         if a.iters >= a.req.maxit or a.refinements >= 60:
             return self._finish(a, "not_converged", rel, t_now)
         # refinement: solve for the float64 residual, relative tolerance rtol of it
         a.refinements += 1
-        a.fd = r
-        a.plan.cg_begin(a.req.lam, r, rtol=self._inner_tol(a.req.rtol, float(np.max(rel))), stream=a.stream)
+        a.fd = a.r
+        a.plan.cg_begin(a.req.lam, a.r, rtol=self._inner_tol(a.req.rtol, float(np.max(rel))), stream=a.stream)
         a.plan.cg_step(self.step_iters, stream=a.stream)
         return None
 

@@ -160,3 +160,40 @@ def test_captured_cg_iterations_equal_plain_launches(precision, nrhs, rtol):
     _, _, c2 = _run_incremental(q, 2.0, fd, [5], s, rtol=rtol)
     assert np.array_equal(c2, results[0][1])
     q.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "mixed"])
+def test_refine_step_never_raises_the_float64_residual(precision):
+    """dwfmm_refine: with a useless correction the float64 residual does not
+    grow (the step length shrinks instead), the updated residual equals
+    f - (K64 + lam I) c recomputed from scratch, and with the float64
+    solution as correction the step length is ~1 and the residual vanishes."""
+    import torch
+    from paper_2402_09531_gb300 import Plan
+    w = di.scaled(di.small_exp_d4(), 2000, nrhs=2)
+    X, f = di.sites_and_rhs(w)
+    lam = 0.5
+    kw = dict(d=4, kernel=w.kernel, gamma=w.gamma, q=4.0, eta=1.0, leaf_size=64, max_rhs=2)
+    p = Plan(precision=precision, **kw)
+    p.tree_build(torch.from_numpy(X).cuda())
+    fd = torch.from_numpy(f).cuda()
+    c = torch.zeros_like(fd)
+    r = fd.clone()
+    junk = torch.from_numpy(np.random.default_rng(9).standard_normal(f.shape) * 1e3).cuda()
+    alpha, rel = p.refine(lam, fd, c, junk, r)
+    assert np.all(rel <= 1.0 + 1e-12)
+    rel_true = p.residual(lam, fd, c)
+    np.testing.assert_allclose(rel, rel_true, rtol=1e-9)
+    p64 = Plan(precision="fp64", **kw)
+    p64.tree_build(torch.from_numpy(X).cuda())
+    exact = torch.zeros_like(fd)
+    st, its, _ = p64.solve(lam, fd, exact, rtol=1e-12, maxit=2000)
+    assert st == 0
+    # correction = exact - c: the step should take it whole
+    corr = exact - c
+    torch.cuda.synchronize()
+    alpha2, rel2 = p.refine(lam, fd, c, corr, r)
+    np.testing.assert_allclose(alpha2, 1.0, atol=1e-6)
+    assert np.all(rel2 <= 1e-9)
+    p.close()
+    p64.close()
