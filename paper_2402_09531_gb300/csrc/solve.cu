@@ -63,10 +63,6 @@ __global__ void k_axpby(const double* x, double* y, const double* z, const doubl
   y[o] = v;
 }
 
-struct Vecs {
-  double *c, *r, *p, *ap, *part, *dot, *coef;
-};
-
 void dots(Plan& P, const double* a, const double* b, int64_t n, int64_t ld, int R, double* part,
           double* out_dev, double* out_host) {
   dim3 grid(kDotBlocks, R);
@@ -85,72 +81,41 @@ void apply_op(Plan& P, const double* v, double* out, int R, double lam, bool fp6
     k_axpby<<<ceil_div(n * R, 256), 256, 0, P.stream>>>(v, out, nullptr, nullptr, 1.0, nullptr, 0.0, n, n, R, lam);
 }
 
-// Plain CG on (K_tilde + lam I) x = b with x0 = 0, columns independent.
-// Returns iterations; per-column status in st (0 ok, 1 breakdown, 2 not converged).
-int cg(Plan& P, Vecs& V, const double* b, double* x, int R, double lam, double rtol, int maxit,
-       bool fp64, std::vector<int>& st) {
-  const int64_t n = P.N;
-  const int64_t nr = n * R;
-  std::vector<double> rr(R), rr_new(R), pap(R), bn(R), alpha(R), beta(R);
-  DW_CUDA(cudaMemsetAsync(x, 0, nr * sizeof(double), P.stream));
-  DW_CUDA(cudaMemcpyAsync(V.r, b, nr * sizeof(double), cudaMemcpyDeviceToDevice, P.stream));
-  DW_CUDA(cudaMemcpyAsync(V.p, b, nr * sizeof(double), cudaMemcpyDeviceToDevice, P.stream));
-  dots(P, V.r, V.r, n, n, R, V.part, V.dot, rr.data());
-  st.assign(R, 2);
-  std::vector<char> active(R, 1);
-  for (int r = 0; r < R; ++r) {
-    bn[r] = std::sqrt(rr[r]);
-    if (bn[r] == 0.0 || std::sqrt(rr[r]) <= rtol * bn[r]) {
-      active[r] = 0;
-      st[r] = 0;
-    }
-  }
-  int it = 0;
-  for (; it < maxit; ++it) {
-    bool any = false;
-    for (int r = 0; r < R; ++r) any |= active[r] != 0;
-    if (!any) break;
-    apply_op(P, V.p, V.ap, R, lam, fp64);
-    dots(P, V.p, V.ap, n, n, R, V.part, V.dot, pap.data());
-    for (int r = 0; r < R; ++r) {
-      alpha[r] = 0.0;
-      if (!active[r]) continue;
-      if (pap[r] == 0.0 || !std::isfinite(pap[r])) {   // negative curvature is tolerated
-        active[r] = 0;
-        st[r] = 1;
-        continue;
-      }
-      alpha[r] = rr[r] / pap[r];
-    }
-    DW_CUDA(cudaMemcpyAsync(V.coef, alpha.data(), R * sizeof(double), cudaMemcpyHostToDevice, P.stream));
-    // x += alpha p ; r -= alpha Ap
-    k_axpby<<<ceil_div(nr, 256), 256, 0, P.stream>>>(V.p, x, nullptr, V.coef, 1.0, nullptr, 0.0, n, n, R, 1.0);
-    k_axpby<<<ceil_div(nr, 256), 256, 0, P.stream>>>(V.ap, V.r, nullptr, V.coef, 1.0, nullptr, 0.0, n, n, R, -1.0);
-    dots(P, V.r, V.r, n, n, R, V.part, V.dot, rr_new.data());
-    for (int r = 0; r < R; ++r) {
-      beta[r] = 0.0;
-      if (!active[r]) continue;
-      if (std::sqrt(rr_new[r]) <= rtol * bn[r]) {
-        active[r] = 0;
-        st[r] = 0;
-      }
-      beta[r] = rr_new[r] / rr[r];
-      rr[r] = rr_new[r];
-    }
-    DW_CUDA(cudaMemcpyAsync(V.coef, beta.data(), R * sizeof(double), cudaMemcpyHostToDevice, P.stream));
-    // p = r + beta p
-    k_axpby<<<ceil_div(nr, 256), 256, 0, P.stream>>>(V.r, V.p, nullptr, nullptr, 0.0, V.coef, 0.0, n, n, R, 1.0);
-  }
-  DW_CUDA(cudaGetLastError());
-  return it;
-}
-
 }  // namespace
 
 // One refinement step with a minimal-residual length (defined with the
 // device-side CG helpers below): c += alpha delta, r -= alpha (A64 delta).
 void refine_step(Plan& P, double lam, double* c, const double* delta, double* r, int R, double* w,
                  double* part, double* dev3);
+
+// CG from x = 0 on (K_tilde + lam I) x = b (device, compact) with the
+// device-side iteration of dwfmm_cg_step (scalars on the GPU, iterations
+// replayed from a captured graph), checking the status snapshot every
+// kSolveChunk iterations; the solution stays in P.cg_c.  st per column:
+// 0 converged, 1 breakdown, 2 not converged.  Returns the largest iteration
+// count.
+int cg_dev(Plan& P, const double* b, int R, double lam, double rtol, int maxit, std::vector<int>& st) {
+  constexpr int kSolveChunk = 16;
+  cg_begin(P, lam, b, R, P.N, rtol);
+  CgState& S = P.cgs;
+  st.assign(R, 2);
+  int done = 0, its = 0;
+  while (done < maxit) {
+    const int k = std::min(kSolveChunk, maxit - done);
+    cg_step(P, k);
+    done += k;
+    DW_CUDA(cudaEventSynchronize(S.ev));
+    bool all = true;
+    for (int r = 0; r < R; ++r) all &= S.h_snap[r] != 0;
+    if (all) break;
+  }
+  for (int r = 0; r < R; ++r) {
+    const int code = S.h_snap[r];
+    st[r] = code == 1 ? 0 : (code == 2 ? 1 : 2);
+    its = std::max(its, S.h_snap[R + r]);
+  }
+  return its;
+}
 
 dwfmm_status solve(Plan& P, double lam, const double* f, double* c, int R, int64_t ld, double rtol,
                    int maxit, int* iters, double* relres) {
@@ -162,26 +127,25 @@ dwfmm_status solve(Plan& P, double lam, const double* f, double* c, int R, int64
       for (int r = 0; r < R; ++r) relres[r] = 0.0;
     return DWFMM_OK;
   }
-  P.cg_r.alloc(nr);
-  P.cg_p.alloc(nr);
-  P.cg_ap.alloc(nr);
-  P.cg_c.alloc(nr);
-  P.cg_f.alloc(nr);
   P.cg_tmp.alloc(nr);
   P.cg_dot.alloc(static_cast<size_t>(kDotBlocks) * R + 8 * R + 8);
-  Vecs V{P.cg_c.p, P.cg_r.p, P.cg_p.p, P.cg_ap.p, P.cg_dot.p, P.cg_dot.p + kDotBlocks * R,
-         P.cg_dot.p + kDotBlocks * R + R};
-  // compact copy of f (leading dimension n)
-  DW_CUDA(cudaMemcpy2DAsync(P.cg_f.p, n * sizeof(double), f, ld * sizeof(double), n * sizeof(double), R,
+  double* part = P.cg_dot.p;
+  double* dot = part + static_cast<size_t>(kDotBlocks) * R;
+  // f (compact) and the solution live outside the CG's own buffers
+  DBuf<double> fc, x;
+  fc.alloc(nr);
+  x.alloc(nr);
+  DW_CUDA(cudaMemcpy2DAsync(fc.p, n * sizeof(double), f, ld * sizeof(double), n * sizeof(double), R,
                             cudaMemcpyDeviceToDevice, P.stream));
   std::vector<double> fn2(R), res2(R);
-  dots(P, P.cg_f.p, P.cg_f.p, n, n, R, V.part, V.dot, fn2.data());
+  dots(P, fc.p, fc.p, n, n, R, part, dot, fn2.data());
   const bool fp64 = P.prec == DWFMM_P_FP64;
   int total_it = 0;
   std::vector<int> st;
   dwfmm_status status = DWFMM_OK;
   if (fp64) {
-    total_it = cg(P, V, P.cg_f.p, V.c, R, lam, rtol, maxit, true, st);
+    total_it = cg_dev(P, fc.p, R, lam, rtol, maxit, st);
+    DW_CUDA(cudaMemcpyAsync(x.p, P.cg_c.p, nr * sizeof(double), cudaMemcpyDeviceToDevice, P.stream));
     for (int r = 0; r < R; ++r) {
       if (st[r] == 1) status = DWFMM_ERR_BREAKDOWN;
       else if (st[r] == 2 && status == DWFMM_OK) status = DWFMM_ERR_NOT_CONVERGED;
@@ -191,11 +155,10 @@ dwfmm_status solve(Plan& P, double lam, const double* f, double* c, int R, int64
     // with alpha = 1 where that lowers the float64 residual, else the
     // minimal-residual length (when the float32 operator's error approaches
     // lambda a capped inner CG can return a correction that would raise it)
-    DW_CUDA(cudaMemsetAsync(V.c, 0, nr * sizeof(double), P.stream));
-    DBuf<double> delta, rhs;
-    delta.alloc(nr);
+    DW_CUDA(cudaMemsetAsync(x.p, 0, nr * sizeof(double), P.stream));
+    DBuf<double> rhs;
     rhs.alloc(nr);
-    DW_CUDA(cudaMemcpyAsync(rhs.p, P.cg_f.p, nr * sizeof(double), cudaMemcpyDeviceToDevice, P.stream));
+    DW_CUDA(cudaMemcpyAsync(rhs.p, fc.p, nr * sizeof(double), cudaMemcpyDeviceToDevice, P.stream));
     // Each inner CG (float32 operator) reduces the float64 residual by at most
     // 1e-3 within at most 400 iterations; the float64 residual then restarts
     // it.  With a small ridge the float32 rounding of the operator (~1e-7 of
@@ -204,7 +167,7 @@ dwfmm_status solve(Plan& P, double lam, const double* f, double* c, int R, int64
     const int inner_maxit = 400;
     status = DWFMM_ERR_NOT_CONVERGED;
     for (int outer = 0; outer < 100 && total_it < maxit; ++outer) {
-      dots(P, rhs.p, rhs.p, n, n, R, V.part, V.dot, res2.data());
+      dots(P, rhs.p, rhs.p, n, n, R, part, dot, res2.data());
       bool done = true;
       double relmax = 0.0;
       for (int r = 0; r < R; ++r) {
@@ -219,12 +182,12 @@ dwfmm_status solve(Plan& P, double lam, const double* f, double* c, int R, int64
       double inner_tol = std::max(rtol, 0.5 * rtol / std::max(relmax, 1e-300));
       if (relmax > rtol / inner_floor) inner_tol = std::max(inner_tol, inner_floor);
       inner_tol = std::min(0.5, inner_tol);
-      const int it = cg(P, V, rhs.p, delta.p, R, lam, inner_tol, std::min(inner_maxit, maxit - total_it), false, st);
+      const int it = cg_dev(P, rhs.p, R, lam, inner_tol, std::min(inner_maxit, maxit - total_it), st);
       total_it += it;
       bool broke = false;
       for (int r = 0; r < R; ++r) broke |= st[r] == 1;
-      double* dev3 = P.cg_dot.p + kDotBlocks * R + 2 * R;
-      refine_step(P, lam, V.c, delta.p, rhs.p, R, P.cg_tmp.p, V.part, dev3);
+      double* dev3 = dot + 2 * R;
+      refine_step(P, lam, x.p, P.cg_c.p, rhs.p, R, P.cg_tmp.p, part, dev3);
       if (broke) {
         // a breakdown of the inner CG is fatal only if its correction did not help
         std::vector<double> alpha(R);
@@ -239,21 +202,23 @@ dwfmm_status solve(Plan& P, double lam, const double* f, double* c, int R, int64
       }
     }
     if (status == DWFMM_ERR_NOT_CONVERGED) {
-      dots(P, rhs.p, rhs.p, n, n, R, V.part, V.dot, res2.data());
+      dots(P, rhs.p, rhs.p, n, n, R, part, dot, res2.data());
       bool done = true;
       for (int r = 0; r < R; ++r) done &= std::sqrt(res2[r]) <= rtol * std::sqrt(fn2[r]) || fn2[r] == 0.0;
       if (done) status = DWFMM_OK;
     }
   }
   // true residual with the float64 operator
-  apply_op(P, V.c, P.cg_tmp.p, R, lam, true);
-  DW_CUDA(cudaMemcpyAsync(P.cg_r.p, P.cg_f.p, nr * sizeof(double), cudaMemcpyDeviceToDevice, P.stream));
-  k_axpby<<<ceil_div(nr, 256), 256, 0, P.stream>>>(P.cg_tmp.p, P.cg_r.p, nullptr, nullptr, 1.0, nullptr, 0.0, n, n, R, -1.0);
-  dots(P, P.cg_r.p, P.cg_r.p, n, n, R, V.part, V.dot, res2.data());
+  DBuf<double> res;
+  res.alloc(nr);
+  apply_op(P, x.p, P.cg_tmp.p, R, lam, true);
+  DW_CUDA(cudaMemcpyAsync(res.p, fc.p, nr * sizeof(double), cudaMemcpyDeviceToDevice, P.stream));
+  k_axpby<<<ceil_div(nr, 256), 256, 0, P.stream>>>(P.cg_tmp.p, res.p, nullptr, nullptr, 1.0, nullptr, 0.0, n, n, R, -1.0);
+  dots(P, res.p, res.p, n, n, R, part, dot, res2.data());
   if (relres)
     for (int r = 0; r < R; ++r) relres[r] = fn2[r] > 0.0 ? std::sqrt(res2[r] / fn2[r]) : 0.0;
   if (iters) *iters = total_it;
-  DW_CUDA(cudaMemcpy2DAsync(c, ld * sizeof(double), V.c, n * sizeof(double), n * sizeof(double), R,
+  DW_CUDA(cudaMemcpy2DAsync(c, ld * sizeof(double), x.p, n * sizeof(double), n * sizeof(double), R,
                             cudaMemcpyDeviceToDevice, P.stream));
   DW_CUDA(cudaStreamSynchronize(P.stream));
   return status;

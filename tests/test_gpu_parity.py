@@ -399,3 +399,29 @@ def test_tensor_index_set_expansion_and_matvec_match_oracle(weights, q):
     torch.cuda.synchronize()
     assert o.rel_err(yd.cpu().numpy(), o.fmm_matvec(pb, f)) <= FP64_TOL
     plan.close()
+
+
+@pytest.mark.parametrize("d,kernel,n_sites", [(7, "matern32", 2600), (12, "gauss", 2600), (15, "exp", 2400),
+                                              (20, "gauss", 2000)])
+def test_mixed_tensor_core_every_padded_dimension(d, kernel, n_sites):
+    """The tensor-core engine is instantiated for padded dimensions 4, 8, 10,
+    12, 16 and 20 (d = 7 pads to 8, 15 to 16): each of those not covered by
+    the workload shapes against the oracle, 16 right-hand sides, leaves of 256
+    (two 128-target tiles per leaf) and a ragged count."""
+    from paper_2402_09531_gb300 import Plan
+    torch = _torch()
+    w = di.Workload(f"dims_{d}", d=d, n=n_sites, gamma=di.gamma_inverse_square(d), kernel=kernel, q=2.0,
+                    leaf=256, eta=1.0, nrhs=16, seed=40 + d)
+    X, f = di.sites_and_rhs(w)
+    wts = o.weights_inv_gamma(w.gamma)
+    pb = o.make_problem(X, kernel, wts, w.q, w.leaf, w.eta)
+    plan = Plan(d=d, kernel=kernel, gamma=w.gamma, q=w.q, eta=w.eta, leaf_size=w.leaf, precision="mixed",
+                max_rhs=16)
+    plan.set_nodes(pb.exp_.nodes)
+    plan.tree_build(torch.from_numpy(X).cuda())
+    xd = torch.from_numpy(f).cuda()
+    yd = torch.full_like(xd, float("nan"))
+    plan.matvec(xd, yd)
+    torch.cuda.synchronize()
+    assert o.rel_err(yd.cpu().numpy(), o.fmm_matvec(pb, f)) <= FP32_TOL
+    plan.close()
