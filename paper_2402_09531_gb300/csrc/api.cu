@@ -63,6 +63,7 @@ void Plan::free_tree() {
   momq32.release();
   bq32.release();
   bqm32.release();
+  near_parts64.release();
   dpad = -1;
 }
 

@@ -274,6 +274,7 @@ struct Plan {
   DBuf<float> xq32, momq32;   // charges interleaved per source, [g][ld][RC]
   DBuf<float> bq32;           // TF32 hi/lo charge blocks for the tensor-core P2P
   DBuf<float> bqm32;          // the same for the tensor-core M2L (moments at the nodes)
+  DBuf<double> near_parts64;  // partial near-field sums of small float64 problems (split lists)
   cudaEvent_t ev_scaled = nullptr;
   DBuf<int> d_err;   // device error flag (3 = a bounded wait timed out)
 

@@ -8,6 +8,9 @@
 // One CTA per target group, one thread per target, sources staged through
 // shared memory in chunks.  This generic kernel serves float64 (parity) and
 // the fallback float32 shapes; the tuned float32 P2P lives in p2p_f32.cu.
+#include <algorithm>
+#include <type_traits>
+
 #include "dwfmm_internal.cuh"
 
 namespace dw {
@@ -37,15 +40,22 @@ struct Side {
 // DM: compile-time bound on d (coordinates beyond d are zero, so the extra
 // terms of the squared distance are exactly 0); RC: right-hand sides held in
 // registers (rows beyond Rc are zero charges).
+// splits > 1: CTA blockIdx.x handles part (blockIdx.x % splits) of group
+// blockIdx.x / splits's list and writes its partial sums to out + part *
+// split_stride (the caller adds the parts in a fixed order).
 template <typename T, int KER, int DM, int RC>
 __global__ void __launch_bounds__(kThreads)
 k_ksum(int first_group, const int32_t* rowptr, const int32_t* col, int d, T inv_sigma,
        const T* tcoord, Side ts, const T* scoord, Side ss, const T* sq, int64_t sq_gstride,
-       int sq_ld, T* out, int64_t o_gstride, int o_ld, int Rc) {
+       int sq_ld, T* out, int64_t o_gstride, int o_ld, int Rc, int splits, int64_t split_stride) {
   __shared__ T sc[DM * kSrcChunk];
   __shared__ T sqs[RC * kSrcChunk];
-  const int g = first_group + blockIdx.x;
-  const int rb = rowptr[g], re = rowptr[g + 1];
+  const int g = first_group + static_cast<int>(blockIdx.x) / splits;
+  const int part = static_cast<int>(blockIdx.x) % splits;
+  const int r0 = rowptr[g], len = rowptr[g + 1] - r0;
+  const int rb = r0 + static_cast<int>((static_cast<int64_t>(len) * part) / splits);
+  const int re = r0 + static_cast<int>((static_cast<int64_t>(len) * (part + 1)) / splits);
+  out += part * split_stride;
   const int tcnt = ts.count ? ts.count[ts.count_off + g] : ts.count_const;
   for (int tb = 0; tb < ts.ld; tb += kThreads) {
     const int i = tb + threadIdx.x;
@@ -96,11 +106,12 @@ template <typename T, int KER, int DM>
 void launch_ksum_rc(int ngroups, int first_group, const int32_t* rowptr, const int32_t* col, int d,
                     T inv_sigma, const T* tcoord, Side ts, const T* scoord, Side ss, const T* sq,
                     int64_t sq_gstride, int sq_ld, T* out, int64_t o_gstride, int o_ld, int Rc,
-                    cudaStream_t s) {
-#define DW_KS(RCV)                                                                                            \
-  k_ksum<T, KER, DM, RCV><<<ngroups, kThreads, 0, s>>>(first_group, rowptr, col, d, inv_sigma, tcoord, ts, \
-                                                       scoord, ss, sq, sq_gstride, sq_ld, out, o_gstride,   \
-                                                       o_ld, Rc)
+                    cudaStream_t s, int splits, int64_t split_stride) {
+#define DW_KS(RCV)                                                                                      \
+  k_ksum<T, KER, DM, RCV><<<ngroups * splits, kThreads, 0, s>>>(first_group, rowptr, col, d, inv_sigma,   \
+                                                                tcoord, ts, scoord, ss, sq, sq_gstride,   \
+                                                                sq_ld, out, o_gstride, o_ld, Rc, splits,  \
+                                                                split_stride)
   if (Rc <= 1) DW_KS(1);
   else if (Rc <= 4) DW_KS(4);
   else DW_KS(16);
@@ -111,11 +122,11 @@ template <typename T, int KER>
 void launch_ksum(int ngroups, int first_group, const int32_t* rowptr, const int32_t* col, int d,
                  T inv_sigma, const T* tcoord, Side ts, const T* scoord, Side ss, const T* sq,
                  int64_t sq_gstride, int sq_ld, T* out, int64_t o_gstride, int o_ld, int Rc,
-                 cudaStream_t s) {
+                 cudaStream_t s, int splits, int64_t split_stride) {
   if (ngroups <= 0) return;
 #define DW_KD(DMV)                                                                                 \
   launch_ksum_rc<T, KER, DMV>(ngroups, first_group, rowptr, col, d, inv_sigma, tcoord, ts, scoord, \
-                              ss, sq, sq_gstride, sq_ld, out, o_gstride, o_ld, Rc, s)
+                              ss, sq, sq_gstride, sq_ld, out, o_gstride, o_ld, Rc, s, splits, split_stride)
   if (d <= 4) DW_KD(4);
   else if (d <= 8) DW_KD(8);
   else if (d <= 12) DW_KD(12);
@@ -129,19 +140,19 @@ template <typename T>
 void dispatch_ksum(int kernel, int ngroups, int first_group, const int32_t* rowptr, const int32_t* col,
                    int d, T inv_sigma, const T* tcoord, Side ts, const T* scoord, Side ss, const T* sq,
                    int64_t sq_gstride, int sq_ld, T* out, int64_t o_gstride, int o_ld, int Rc,
-                   cudaStream_t s) {
+                   cudaStream_t s, int splits = 1, int64_t split_stride = 0) {
   switch (kernel) {
     case DWFMM_K_EXP:
       launch_ksum<T, DWFMM_K_EXP>(ngroups, first_group, rowptr, col, d, inv_sigma, tcoord, ts, scoord, ss,
-                                  sq, sq_gstride, sq_ld, out, o_gstride, o_ld, Rc, s);
+                                  sq, sq_gstride, sq_ld, out, o_gstride, o_ld, Rc, s, splits, split_stride);
       break;
     case DWFMM_K_MATERN32:
       launch_ksum<T, DWFMM_K_MATERN32>(ngroups, first_group, rowptr, col, d, inv_sigma, tcoord, ts, scoord,
-                                       ss, sq, sq_gstride, sq_ld, out, o_gstride, o_ld, Rc, s);
+                                       ss, sq, sq_gstride, sq_ld, out, o_gstride, o_ld, Rc, s, splits, split_stride);
       break;
     default:
       launch_ksum<T, DWFMM_K_GAUSS>(ngroups, first_group, rowptr, col, d, inv_sigma, tcoord, ts, scoord, ss,
-                                    sq, sq_gstride, sq_ld, out, o_gstride, o_ld, Rc, s);
+                                    sq, sq_gstride, sq_ld, out, o_gstride, o_ld, Rc, s, splits, split_stride);
   }
 }
 
@@ -157,13 +168,53 @@ void m2l_impl(Plan& P, int Rc, const T* ynode, const T* mom, T* loc) {
                    static_cast<int64_t>(kRC) * P.n_pad, P.n_pad, Rc, P.stream);
 }
 
+// out[g][r][i] = sum over parts of part[p][g][r][i] in part order (r < Rc).
+__global__ void k_sum_parts(const double* part, int splits, int64_t stride, int64_t n, int64_t o_gstride,
+                            int o_ld, int Rc, double* out) {
+  const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int r = static_cast<int>((t % o_gstride) / o_ld);
+  if (r >= Rc) return;
+  double acc = 0.0;
+  for (int p = 0; p < splits; ++p) acc += part[p * stride + t];
+  out[t] = acc;
+}
+
+int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    DW_CUDA(cudaGetDevice(&dev));
+    DW_CUDA(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+  }
+  return n;
+}
+
 template <typename T>
 void p2p_impl(Plan& P, int Rc, const T* pts, const T* xb, T* ynear, cudaStream_t s) {
   const int64_t gs = static_cast<int64_t>(P.d) * P.m_pad;
   Side side{gs, P.m_pad, P.d_count.p, P.L - 1, 0};
-  dispatch_ksum<T>(P.kernel, P.L, 0, P.d_near_rowptr.p, P.d_near_col.p, P.d, T(1.0 / P.sigma), pts, side,
-                   pts, side, xb, static_cast<int64_t>(kRC) * P.m_pad, P.m_pad, ynear,
-                   static_cast<int64_t>(kRC) * P.m_pad, P.m_pad, Rc, s);
+  const int64_t o_gstride = static_cast<int64_t>(kRC) * P.m_pad;
+  // Small float64 problems: one CTA per leaf would leave most SMs idle (and
+  // GB300's float64 unit is narrow), so each leaf's near list is split over
+  // several CTAs whose partial sums are added in a fixed order.
+  int splits = 1;
+  if (std::is_same<T, double>::value) {
+    const int want = 2 * sm_count();
+    if (P.L < want) splits = std::min(16, (want + P.L - 1) / P.L);
+  }
+  if (splits == 1) {
+    dispatch_ksum<T>(P.kernel, P.L, 0, P.d_near_rowptr.p, P.d_near_col.p, P.d, T(1.0 / P.sigma), pts, side,
+                     pts, side, xb, o_gstride, P.m_pad, ynear, o_gstride, P.m_pad, Rc, s);
+    return;
+  }
+  const int64_t stride = static_cast<int64_t>(P.L) * o_gstride;
+  P.near_parts64.alloc(static_cast<size_t>(splits) * stride);
+  T* part = reinterpret_cast<T*>(P.near_parts64.p);
+  dispatch_ksum<T>(P.kernel, P.L, 0, P.d_near_rowptr.p, P.d_near_col.p, P.d, T(1.0 / P.sigma), pts, side, pts,
+                   side, xb, o_gstride, P.m_pad, part, o_gstride, P.m_pad, Rc, s, splits, stride);
+  k_sum_parts<<<ceil_div(stride, 256), 256, 0, s>>>(reinterpret_cast<const double*>(part), splits, stride, stride,
+                                                     o_gstride, P.m_pad, Rc, reinterpret_cast<double*>(ynear));
 }
 
 }  // namespace
