@@ -7,12 +7,14 @@
 // CUDA cores evaluate E (as in k_sum_f32: scaled coordinates, packed
 // fma.f32x2 distances, one ex2), split it into TF32 hi + lo and store both
 // into tensor memory as the A operand; one thread issues
-// tcgen05.mma.kind::tf32 (M=128 targets, N=16 right-hand sides, K=8
-// sources) with B = the charges, pre-split into TF32 hi + lo in the
-// no-swizzle K-major core-matrix layout and staged by TMA bulk copies.
-// Three products per K step (hi*hi + hi*lo + lo*hi) keep ~2^-20 relative
-// accuracy per term; each source block accumulates into a TMEM tile (FP32),
-// which is read back and folded into Kahan-compensated running sums.
+// tcgen05.mma.kind::tf32 (M=128 targets, K=8 sources) with B = the charges,
+// pre-split into TF32 hi + lo in the no-swizzle K-major core-matrix layout
+// and staged by TMA bulk copies.  The hi and lo charge blocks are adjacent
+// in that layout, so one N=32 product gives E_hi*[q_hi | q_lo] and a second,
+// N=16, adds E_lo*q_hi: three terms (~2^-20 relative each) in two MMAs per
+// K step.  Each source block accumulates into a 32-column TMEM tile (FP32),
+// whose two halves are read back, added and folded into Kahan-compensated
+// running sums.
 //
 // One CTA = 128 targets, warp-specialised: eight compute warps (warps w and
 // w+4 share the TMEM lanes of quadrant w, each evaluating half of every
@@ -21,7 +23,7 @@
 // (stage full / coordinates free / charges free, A full / A empty, D full /
 // D empty), so the compute warps never wait at a CTA-wide barrier inside the
 // loop; the two control threads sleep between polls.  TMEM: two A buffers
-// (2 x 64 columns: 32 sources hi + lo) and two 16-column accumulators, 256
+// (2 x 64 columns: 32 sources hi + lo) and two 32-column accumulators, 256
 // columns allocated.  Every wait is bounded.
 #include <cstdint>
 
@@ -54,8 +56,10 @@ __device__ __forceinline__ float phi_of(float a) {
   return fmaf(r, e, e);
 }
 
-// Instruction descriptor: M = 128 targets, N = 16 right-hand sides.
-constexpr uint32_t kIdesc = idesc_tf32(128, 16);
+// Instruction descriptors: M = 128 targets; N = 32 (the hi and lo charge
+// blocks together) or 16 (hi only).
+constexpr uint32_t kIdesc32 = idesc_tf32(128, 32);
+constexpr uint32_t kIdesc16 = idesc_tf32(128, 16);
 
 // Charges [g][ld][16] (interleaved per source) -> TF32 hi and lo blocks in
 // the K-major core layout: block g = [hi | lo], each 16 x ld, core (nb, kb)
@@ -252,7 +256,7 @@ __global__ void __launch_bounds__(kTcThreads, (D <= 12 ? 2 : 1)) k_sum_tc(TcArgs
       if (bad) atomicExch(a.err, 3);
     }
   } else if (warp == kCompWarps) {
-    // ---- MMA issuer: three TF32 products per 8-source step of every chunk
+    // ---- MMA issuer: two TF32 products per 8-source step of every chunk
     if (lane == 0) {
       bool bad = false;
       int chunk = 0, kb = 0;
@@ -270,7 +274,7 @@ __global__ void __launch_bounds__(kTcThreads, (D <= 12 ? 2 : 1)) k_sum_tc(TcArgs
             break;
           }
           const uint32_t bq_addr = sptr(stage0 + st * stage_bytes + coord_pad);
-          const uint32_t d_tmem = tmem + 128 + 16 * db;
+          const uint32_t d_tmem = tmem + 128 + 32 * db;
           for (int c0 = 0; c0 < s8; c0 += kChunkS) {
             const int ab = chunk & 1;
             if (!wait_ctl(&afull[ab], static_cast<uint32_t>((chunk >> 1) & 1), kMmaFirstNs, kMmaStepNs)) {
@@ -282,12 +286,11 @@ __global__ void __launch_bounds__(kTcThreads, (D <= 12 ? 2 : 1)) k_sum_tc(TcArgs
             const uint32_t a_tmem = tmem + 64 * ab;
             for (int ks = 0; ks < ns; ks += 8) {
               const uint32_t boff = static_cast<uint32_t>(((c0 + ks) / 4) * 128);
-              const u64 bhi = smem_desc(bq_addr + boff, 128, static_cast<uint32_t>(ld * 32));
-              const u64 blo = smem_desc(bq_addr + static_cast<uint32_t>(16 * ld * 4) + boff, 128,
-                                        static_cast<uint32_t>(ld * 32));
-              mma_tf32(d_tmem, a_tmem + ks, bhi, kIdesc, (c0 + ks) > 0 ? 1u : 0u);
-              mma_tf32(d_tmem, a_tmem + ks, blo, kIdesc, 1u);
-              mma_tf32(d_tmem, a_tmem + 32 + ks, bhi, kIdesc, 1u);
+              // rows 0..15 of B = q_hi, rows 16..31 = q_lo (the lo block
+              // starts 16 * ld floats = two 8-row groups after the hi block)
+              const u64 bq = smem_desc(bq_addr + boff, 128, static_cast<uint32_t>(ld * 32));
+              mma_tf32(d_tmem, a_tmem + ks, bq, kIdesc32, (c0 + ks) > 0 ? 1u : 0u);
+              mma_tf32(d_tmem, a_tmem + 32 + ks, bq, kIdesc16, 1u);
             }
             mma_commit(&aempty[ab]);
             ++chunk;
@@ -333,11 +336,11 @@ __global__ void __launch_bounds__(kTcThreads, (D <= 12 ? 2 : 1)) k_sum_tc(TcArgs
         return;
       }
       asm volatile("tcgen05.fence::after_thread_sync;");
-      uint32_t dv[8];
-      tmem_ld8(lane_base + 128 + 16 * db + 8 * hf, dv);
+      uint32_t dv[8], dl[8];
+      tmem_ld8x2(lane_base + 128 + 32 * db + 8 * hf, lane_base + 128 + 32 * db + 16 + 8 * hf, dv, dl);
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
-        const float y = __uint_as_float(dv[r]) - comp[r];
+        const float y = (__uint_as_float(dv[r]) + __uint_as_float(dl[r])) - comp[r];
         const float s = acc[r] + y;
         comp[r] = (s - acc[r]) - y;
         acc[r] = s;
