@@ -1,6 +1,7 @@
 // extern "C" entry points of include/dwfmm.h.  Validates arguments, stages
 // host buffers through device memory, and maps internal errors to status
 // codes; every numerical step is a kernel launched from the other files.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -263,6 +264,22 @@ dwfmm_status dwfmm_tree_build(dwfmm_plan plan, const double* pts, int64_t n, int
     dw::build_tree(P, dev, n, ld);
     dw::build_lists(P);
     dw::build_cluster_data(P);
+    // bound of |x'|^2 = |x|^2 log2(e) / (2 sigma^2) over the root box, which
+    // holds every site and every interpolation node
+    P.gauss_fact = false;
+    if (P.kernel == DWFMM_K_GAUSS && n > 0) {
+      std::vector<double> lo(P.d), hi(P.d);
+      DW_CUDA(cudaMemcpyAsync(lo.data(), P.d_lo.p, sizeof(double) * P.d, cudaMemcpyDeviceToHost, P.stream));
+      DW_CUDA(cudaMemcpyAsync(hi.data(), P.d_hi.p, sizeof(double) * P.d, cudaMemcpyDeviceToHost, P.stream));
+      DW_CUDA(cudaStreamSynchronize(P.stream));
+      const double s2 = 1.4426950408889634 / (2.0 * P.sigma * P.sigma);
+      double b = 0.0;
+      for (int k = 0; k < P.d; ++k) {
+        const double m = std::max(std::fabs(lo[k]), std::fabs(hi[k]));
+        b += m * m * s2;
+      }
+      P.gauss_fact = b <= 30.0;
+    }
     P.have_tree = true;
     return DWFMM_OK;
   });

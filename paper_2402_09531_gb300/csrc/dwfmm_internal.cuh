@@ -239,6 +239,9 @@ struct Plan {
 
   // tree (Sec. 5.1)
   bool have_tree = false;
+  // Gaussian kernel with every scaled squared norm |x'|^2 of the root box at
+  // most 30: the tensor-core near field may evaluate it in factored form
+  bool gauss_fact = false;
   int64_t N = 0;
   int J = -1, L = 0, C = 0, m_pad = 0, jmin = 0;
   std::vector<int32_t> h_begin, h_count;
@@ -333,7 +336,7 @@ void ensure_sum_attrs();
 bool sum_tc(int D, int kernel, const float* tgt, int64_t tgt_gstride, const float* src, int64_t src_gstride,
             const float* xq16, int64_t groups_src, DBuf<float>& bq_scratch, float* out, int64_t out_gstride,
             const int32_t* rowptr, const int32_t* col, const int32_t* count, int count_off, int count_const,
-            int first, int ngroups, int ld, int Rc, int* err, cudaStream_t s);
+            int first, int ngroups, int ld, int Rc, bool gauss_factored, int* err, cudaStream_t s);
 void evaluate(Plan& P, const double* tgt, int64_t nt, int64_t ldt, const double* c, int64_t ldc, double* out,
               int64_t ldo, int R);
 void eval_f64(Plan& P, const double* tgt64, int G, const int32_t* rowptr, const int32_t* col, int Rc, double* out,

@@ -501,7 +501,7 @@ bool p2p_f32_tuned(Plan& P, int Rc, cudaStream_t s) {
       sum_tc(D, P.kernel, P.d_ptsk.p, static_cast<int64_t>(D + 1) * P.m_pad, P.d_ptsk.p,
              static_cast<int64_t>(D + 1) * P.m_pad, P.xq32.p, P.L, P.bq32, P.ynear32.p,
              static_cast<int64_t>(kRC) * P.m_pad, P.d_near_rowptr.p, P.d_near_col.p, P.d_count.p, P.L - 1, 0, 0,
-             P.L, P.m_pad, Rc, P.d_err.p, s))
+             P.L, P.m_pad, Rc, P.gauss_fact, P.d_err.p, s))
     return true;
   SumArgs a{};
   a.tgt = P.d_ptsk.p;
@@ -583,7 +583,7 @@ bool m2l_f32_tuned(Plan& P, int Rc) {
       sum_tc(D, P.kernel, P.d_ynodek.p, static_cast<int64_t>(D + 1) * P.n_pad, P.d_ynodek.p,
              static_cast<int64_t>(D + 1) * P.n_pad, P.momq32.p, P.C, P.bqm32, P.loc32.p,
              static_cast<int64_t>(kRC) * P.n_pad, P.d_far_rowptr.p, P.d_far_col.p, nullptr, 0, P.n, first,
-             P.C - first, P.n_pad, Rc, P.d_err.p, P.stream))
+             P.C - first, P.n_pad, Rc, P.gauss_fact, P.d_err.p, P.stream))
     return true;
   SumArgs a{};
   a.tgt = P.d_ynodek.p;

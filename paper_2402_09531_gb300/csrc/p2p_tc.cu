@@ -64,15 +64,20 @@ constexpr uint32_t kIdesc16 = idesc_tf32(128, 16);
 // Charges [g][ld][16] (interleaved per source) -> TF32 hi and lo blocks in
 // the K-major core layout: block g = [hi | lo], each 16 x ld, core (nb, kb)
 // at kb * 128 + nb * (ld * 32) bytes, row i of a core at i * 16 bytes.
-__global__ void k_make_bq(const float* xq, int64_t groups, int ld, float* bq) {
+// Gaussian kernel: each charge carries its source's factor 2^(-|s'|^2)
+// (norm row D of the scaled source block).
+__global__ void k_make_bq(const float* xq, int64_t groups, int ld, const float* src, int64_t src_gstride, int D,
+                          int gauss, float* bq) {
   const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t >= groups * ld * 16) return;
   const int r = static_cast<int>(t % 16);
   const int64_t gs = t / 16;
   const int s = static_cast<int>(gs % ld);
   const int64_t g = gs / ld;
+  float v = xq[t];
+  if (gauss) v *= exp2f(-src[g * src_gstride + static_cast<int64_t>(D) * ld + s]);
   uint32_t hi, lo;
-  split_tf32(xq[t], hi, lo);
+  split_tf32(v, hi, lo);
   const int64_t off = (static_cast<int64_t>(s / 4) * 128 + (r / 8) * static_cast<int64_t>(ld) * 32 + (r % 8) * 16 +
                        (s % 4) * 4) / 4;
   float* blk = bq + g * (2 * 16 * static_cast<int64_t>(ld));
@@ -100,20 +105,23 @@ struct TcArgs {
   int* err;
 };
 
-// 8 pairs (one target, sources j..j+7 of the stage): phi, TF32 split.
+// 8 pairs (one target, sources j..j+7 of the stage): phi, TF32 split.  The
+// Gaussian is evaluated in factored form, E' = 2^(2 x'.s'): the factors
+// 2^(-|x'|^2) and 2^(-|s'|^2) sit on the sums and the charges.
 template <int D, int KER>
-__device__ __forceinline__ void eval8(const float* sc, int j, const u64* xt2, u64 mnt2, uint32_t* hi,
-                                      uint32_t* lo) {
+__device__ __forceinline__ void eval8(const float* sc, int j, const u64* xt2, uint32_t* hi, uint32_t* lo) {
   u64 p[4];
   if (KER == DWFMM_K_GAUSS) {
-    const ulonglong2 n0 = *reinterpret_cast<const ulonglong2*>(sc + D * kRow + j);
-    const ulonglong2 n1 = *reinterpret_cast<const ulonglong2*>(sc + D * kRow + j + 4);
-    p[0] = sub2(mnt2, n0.x);
-    p[1] = sub2(mnt2, n0.y);
-    p[2] = sub2(mnt2, n1.x);
-    p[3] = sub2(mnt2, n1.y);
+    {
+      const ulonglong2 v0 = *reinterpret_cast<const ulonglong2*>(sc + j);
+      const ulonglong2 v1 = *reinterpret_cast<const ulonglong2*>(sc + j + 4);
+      p[0] = mul2(xt2[0], v0.x);
+      p[1] = mul2(xt2[0], v0.y);
+      p[2] = mul2(xt2[0], v1.x);
+      p[3] = mul2(xt2[0], v1.y);
+    }
 #pragma unroll
-    for (int k = 0; k < D; ++k) {
+    for (int k = 1; k < D; ++k) {
       const ulonglong2 v0 = *reinterpret_cast<const ulonglong2*>(sc + k * kRow + j);
       const ulonglong2 v1 = *reinterpret_cast<const ulonglong2*>(sc + k * kRow + j + 4);
       p[0] = fma2(xt2[k], v0.x, p[0]);
@@ -318,8 +326,8 @@ __global__ void __launch_bounds__(kTcThreads, (D <= 12 ? 2 : 1)) k_sum_tc(TcArgs
       const float v = (KER == DWFMM_K_GAUSS) ? 2.0f * tp[k * ld] : tp[k * ld];
       xt2[k] = pk(v, v);
     }
-    const float ntv = (KER == DWFMM_K_GAUSS) ? -tp[D * ld] : 0.0f;
-    const u64 mnt2 = pk(ntv, ntv);
+    // target factor of the factored Gaussian
+    const float tfac = (KER == DWFMM_K_GAUSS) ? exp2f(-tp[D * ld]) : 1.0f;
     float acc[8], comp[8];
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
@@ -372,13 +380,13 @@ __global__ void __launch_bounds__(kTcThreads, (D <= 12 ? 2 : 1)) k_sum_tc(TcArgs
         const uint32_t col = static_cast<uint32_t>(64 * ab + 16 * hf);
         if (jn >= 16) {
           uint32_t hi[16], lo[16];
-          eval8<D, KER>(sc, j0, xt2, mnt2, hi, lo);
-          eval8<D, KER>(sc, j0 + 8, xt2, mnt2, hi + 8, lo + 8);
+          eval8<D, KER>(sc, j0, xt2, hi, lo);
+          eval8<D, KER>(sc, j0 + 8, xt2, hi + 8, lo + 8);
           tmem_st16(lane_base + col, hi);
           tmem_st16(lane_base + col + 32, lo);
         } else if (jn > 0) {
           uint32_t hi[8], lo[8];
-          eval8<D, KER>(sc, j0, xt2, mnt2, hi, lo);
+          eval8<D, KER>(sc, j0, xt2, hi, lo);
           tmem_st8(lane_base + col, hi);
           tmem_st8(lane_base + col + 32, lo);
         }
@@ -405,7 +413,7 @@ __global__ void __launch_bounds__(kTcThreads, (D <= 12 ? 2 : 1)) k_sum_tc(TcArgs
       float* op = a.out + g * a.out_gstride + ti;
 #pragma unroll
       for (int r = 0; r < 8; ++r)
-        if (8 * hf + r < a.Rc) op[(8 * hf + r) * ld] = acc[r];
+        if (8 * hf + r < a.Rc) op[(8 * hf + r) * ld] = (KER == DWFMM_K_GAUSS) ? acc[r] * tfac : acc[r];
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -446,12 +454,17 @@ bool g_tc_attrs = false;
 
 // Tensor-core kernel summation over (target group, source group) lists.
 // bq_scratch receives the TF32 hi/lo charge blocks.  Returns false when the
-// shape is not covered (the caller then runs the CUDA-core kernel).
+// shape is not covered (the caller then runs the CUDA-core kernel): a
+// Gaussian needs gauss_factored, i.e. every scaled squared norm |x'|^2 of
+// the sites and nodes small enough that 2^(2 x'.s') and 2^(-|s'|^2) stay
+// well inside the float32 range.
 bool sum_tc(int D, int kernel, const float* tgt, int64_t tgt_gstride, const float* src, int64_t src_gstride,
             const float* xq16, int64_t groups_src, DBuf<float>& bq_scratch, float* out, int64_t out_gstride,
             const int32_t* rowptr, const int32_t* col, const int32_t* count, int count_off, int count_const,
-            int first, int ngroups, int ld, int Rc, int* err, cudaStream_t s) {
+            int first, int ngroups, int ld, int Rc, bool gauss_factored, int* err, cudaStream_t s) {
   if (ld % 8 != 0 || ld > kRow || (D != 4 && D != 8 && D != 10 && D != 12 && D != 16 && D != 20)) return false;
+  const bool gauss = kernel == DWFMM_K_GAUSS;
+  if (gauss && !gauss_factored) return false;
   const size_t smem = tc_smem(D, ld);
   if (smem > 200 * 1024) return false;
   if (!g_tc_attrs) {
@@ -466,7 +479,8 @@ bool sum_tc(int D, int kernel, const float* tgt, int64_t tgt_gstride, const floa
   }
   bq_scratch.alloc(static_cast<size_t>(groups_src) * 2 * 16 * ld);
   const int64_t nq = groups_src * ld * 16;
-  k_make_bq<<<ceil_div(nq, 256), 256, 0, s>>>(xq16, groups_src, ld, bq_scratch.p);
+  k_make_bq<<<ceil_div(nq, 256), 256, 0, s>>>(xq16, groups_src, ld, src, src_gstride, D, gauss ? 1 : 0,
+                                               bq_scratch.p);
   TcArgs a{};
   a.tgt = tgt;
   a.tgt_gstride = tgt_gstride;

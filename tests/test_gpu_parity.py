@@ -369,6 +369,29 @@ def test_mixed_tensor_core_d10_workload_shape():
     assert o.rel_err(y, o.fmm_matvec(pb, f)) <= FP32_TOL
 
 
+@pytest.mark.parametrize("sigma", [0.1, 0.35])
+def test_mixed_gauss_factored_range(sigma):
+    """The tensor-core near field evaluates the Gaussian as 2^(2 x'.s') with
+    the factors 2^(-|x'|^2), 2^(-|s'|^2) on the sums and the charges, where
+    x' = x sqrt(log2 e / (2 sigma^2)), only if |x'|^2 <= 30 on the root box.
+    sigma = 0.35 is inside that range (bound ~7.8), sigma = 0.1 outside it
+    (bound ~96: the CUDA-core kernel runs instead); both match the oracle."""
+    torch = _torch()
+    w = di.Workload(f"gauss_sigma_{sigma}", d=4, n=3001, gamma=np.array([1.0, 0.5, 0.25, 0.125]),
+                    kernel="gauss", q=4.0, leaf=64, eta=1.0, nrhs=16, sigma=sigma, seed=33)
+    X, f = di.sites_and_rhs(w)
+    pb = o.make_problem(X, w.kernel, o.weights_inv_gamma(w.gamma), w.q, w.leaf, w.eta, w.sigma)
+    plan = _plan(w, "mixed", max_rhs=16)
+    plan.set_nodes(pb.exp_.nodes)
+    plan.tree_build(torch.from_numpy(X).cuda())
+    xd = torch.from_numpy(f).cuda()
+    yd = torch.full_like(xd, float("nan"))
+    plan.matvec(xd, yd)
+    torch.cuda.synchronize()
+    assert o.rel_err(yd.cpu().numpy(), o.fmm_matvec(pb, f)) <= FP32_TOL
+    plan.close()
+
+
 # ---------------------------------------------------------------------------
 # Tensor-product index set (Sec. 6.1's TPI) as a comparison mode
 # ---------------------------------------------------------------------------
