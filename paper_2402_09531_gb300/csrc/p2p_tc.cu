@@ -22,7 +22,8 @@
 // lane 0 issues the TMA loads.  The roles hand over through mbarriers only
 // (stage full / coordinates free / charges free, A full / A empty, D full /
 // D empty), so the compute warps never wait at a CTA-wide barrier inside the
-// loop; the two control threads sleep between polls.  TMEM: two A buffers
+// loop; every waiting thread sleeps in the barrier (mbarrier.try_wait with
+// a suspend-time hint) until the phase completes.  TMEM: two A buffers
 // (2 x 64 columns: 32 sources hi + lo) and two 32-column accumulators, 256
 // columns allocated.  Every wait is bounded.
 #include <cstdint>
@@ -40,11 +41,6 @@ constexpr int kCompWarps = 8;
 constexpr int kTcThreads = (kCompWarps + 2) * 32;   // compute warps, MMA warp, TMA warp
 constexpr int kChunkS = 32;                          // sources per A buffer
 constexpr int kTmemCols = 256;
-// Sleeps of the control threads between polls.  The MMA thread polls
-// briskly (the compute warps wait for its commits two chunks later); the TMA
-// thread sleeps longer first (about half a block's evaluation time).
-constexpr uint32_t kMmaFirstNs = 64, kMmaStepNs = 64;
-constexpr uint32_t kTmaFirstNs = 2000, kTmaStepNs = 250;
 constexpr int kRow = 256;                // shared-memory row stride (floats) of the coordinates
 
 template <int KER>
@@ -222,7 +218,7 @@ __global__ void __launch_bounds__(kTcThreads, (D <= 12 ? 2 : 1)) k_sum_tc(TcArgs
         const int st = b & 1;
         if (b >= 2) {
           const uint32_t par = static_cast<uint32_t>(((b - 2) >> 1) & 1);
-          if (!wait_ctl(&cfree[st], par, kTmaFirstNs, kTmaStepNs) || !wait_ctl(&bqfree[st], par, kTmaFirstNs, kTmaStepNs)) {
+          if (!wait_sleep(&cfree[st], par) || !wait_sleep(&bqfree[st], par)) {
             bad = true;
             break;
           }
@@ -260,7 +256,7 @@ __global__ void __launch_bounds__(kTcThreads, (D <= 12 ? 2 : 1)) k_sum_tc(TcArgs
       }
       // the copies in flight land before the CTA exits
       for (int b = issued >= 2 ? issued - 2 : 0; b < issued; ++b)
-        (void)wait_ctl(&full[b & 1], static_cast<uint32_t>((b >> 1) & 1), kTmaStepNs, kTmaStepNs);
+        (void)wait_sleep(&full[b & 1], static_cast<uint32_t>((b >> 1) & 1));
       if (bad) atomicExch(a.err, 3);
     }
   } else if (warp == kCompWarps) {
@@ -270,14 +266,14 @@ __global__ void __launch_bounds__(kTcThreads, (D <= 12 ? 2 : 1)) k_sum_tc(TcArgs
       int chunk = 0, kb = 0;
       for (int b = 0; b < nb && !bad; ++b) {
         const int st = b & 1;
-        if (!wait_ctl(&full[st], static_cast<uint32_t>((b >> 1) & 1), kMmaStepNs, kMmaStepNs)) {
+        if (!wait_sleep(&full[st], static_cast<uint32_t>((b >> 1) & 1))) {
           bad = true;
           break;
         }
         const int s8 = stage_s8[st];
         if (s8 > 0) {
           const int db = kb & 1;
-          if (kb >= 2 && !wait_ctl(&dempty[db], static_cast<uint32_t>(((kb - 2) >> 1) & 1), kMmaStepNs, kMmaStepNs)) {
+          if (kb >= 2 && !wait_sleep(&dempty[db], static_cast<uint32_t>(((kb - 2) >> 1) & 1))) {
             bad = true;
             break;
           }
@@ -285,7 +281,7 @@ __global__ void __launch_bounds__(kTcThreads, (D <= 12 ? 2 : 1)) k_sum_tc(TcArgs
           const uint32_t d_tmem = tmem + 128 + 32 * db;
           for (int c0 = 0; c0 < s8; c0 += kChunkS) {
             const int ab = chunk & 1;
-            if (!wait_ctl(&afull[ab], static_cast<uint32_t>((chunk >> 1) & 1), kMmaFirstNs, kMmaStepNs)) {
+            if (!wait_sleep(&afull[ab], static_cast<uint32_t>((chunk >> 1) & 1))) {
               bad = true;
               break;
             }
@@ -310,7 +306,7 @@ __global__ void __launch_bounds__(kTcThreads, (D <= 12 ? 2 : 1)) k_sum_tc(TcArgs
         mma_commit(&bqfree[st]);
       }
       mma_commit(fin);
-      (void)wait_ctl(fin, 0u, kMmaStepNs, kMmaStepNs);
+      (void)wait_sleep(fin, 0u);
       if (bad) atomicExch(a.err, 3);
     }
   } else {
@@ -338,7 +334,7 @@ __global__ void __launch_bounds__(kTcThreads, (D <= 12 ? 2 : 1)) k_sum_tc(TcArgs
     // fold accumulator k (this warp's 8 right-hand sides) into the sums
     auto fold = [&](int k) {
       const int db = k & 1;
-      const bool ok = wait_parity(&dfull[db], static_cast<uint32_t>((k >> 1) & 1));
+      const bool ok = wait_sleep(&dfull[db], static_cast<uint32_t>((k >> 1) & 1));
       if (__any_sync(0xffffffffu, !ok)) {
         bad = true;
         return;
@@ -360,7 +356,7 @@ __global__ void __launch_bounds__(kTcThreads, (D <= 12 ? 2 : 1)) k_sum_tc(TcArgs
     int chunk = 0, kb = 0;
     for (int b = 0; b < nb; ++b) {
       const int st = b & 1;
-      const bool ok = wait_parity(&full[st], static_cast<uint32_t>((b >> 1) & 1));
+      const bool ok = wait_sleep(&full[st], static_cast<uint32_t>((b >> 1) & 1));
       if (__any_sync(0xffffffffu, !ok)) {
         bad = true;
         break;
@@ -369,7 +365,7 @@ __global__ void __launch_bounds__(kTcThreads, (D <= 12 ? 2 : 1)) k_sum_tc(TcArgs
       const int s8 = stage_s8[st];
       for (int c0 = 0; c0 < s8; c0 += kChunkS) {
         const int ab = chunk & 1;
-        const bool okA = chunk < 2 || wait_parity(&aempty[ab], static_cast<uint32_t>(((chunk - 2) >> 1) & 1));
+        const bool okA = chunk < 2 || wait_sleep(&aempty[ab], static_cast<uint32_t>(((chunk - 2) >> 1) & 1));
         if (__any_sync(0xffffffffu, !okA)) {
           bad = true;
           break;

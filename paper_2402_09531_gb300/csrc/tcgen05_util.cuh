@@ -1,7 +1,7 @@
-// Device helpers shared by the tensor-core kernel summations (sm_103a):
-// mbarrier waits with iteration limits, tcgen05 MMA / commit / TMEM
-// load-store wrappers, shared-memory operand descriptors, packed float32x2
-// arithmetic and the TF32 hi/lo splits.  Inline PTX only.
+// Device helpers of the tensor-core kernel summation (sm_103a): bounded
+// mbarrier waits, tcgen05 MMA / commit / TMEM load-store wrappers,
+// shared-memory operand descriptors, packed float32x2 arithmetic and the
+// TF32 hi/lo splits.  Inline PTX only.
 #pragma once
 
 #include <cstdint>
@@ -11,43 +11,21 @@ namespace tc {
 
 typedef unsigned long long u64;
 
-constexpr int kWaitPolls = 1 << 22;   // try_wait polls of a bounded wait (a few seconds at most)
-constexpr int kCtlPolls = 1 << 24;    // test_wait polls of a control thread, each followed by a sleep
-
 __device__ __forceinline__ uint32_t sptr(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
 
-// Bounded wait for the phase of the given parity; false if it gave up.
-__device__ __forceinline__ bool wait_parity(uint64_t* bar, uint32_t parity) {
+// Bounded wait that suspends in the barrier (up to hint_ns per poll, woken
+// when the phase completes), so that a waiting warp takes no issue slots.
+constexpr int kSleepPolls = 1 << 18;
+__device__ __forceinline__ bool wait_sleep(uint64_t* bar, uint32_t parity, uint32_t hint_ns = 20000u) {
   const uint32_t a = sptr(bar);
-  for (int it = 0; it < kWaitPolls; ++it) {
+  for (int it = 0; it < kSleepPolls; ++it) {
     uint32_t done;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}"
         : "=r"(done)
-        : "r"(a), "r"(parity)
+        : "r"(a), "r"(parity), "r"(hint_ns)
         : "memory");
     if (done) return true;
-  }
-  return false;
-}
-
-__device__ __forceinline__ bool test_parity(uint64_t* bar, uint32_t parity) {
-  uint32_t done;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(done)
-      : "r"(sptr(bar)), "r"(parity)
-      : "memory");
-  return done != 0;
-}
-
-// Wait of a control thread: test, sleep first_ns, then test every step_ns.
-__device__ __forceinline__ bool wait_ctl(uint64_t* bar, uint32_t parity, uint32_t first_ns, uint32_t step_ns) {
-  if (test_parity(bar, parity)) return true;
-  __nanosleep(first_ns);
-  for (int it = 0; it < kCtlPolls; ++it) {
-    if (test_parity(bar, parity)) return true;
-    __nanosleep(step_ns);
   }
   return false;
 }
