@@ -299,7 +299,7 @@ def run_ours(args):
     launches = sum(v[1] for k, v in phases.items() if k != "matvec")
     # DRAM bytes per P2P launch from a 1-pass ncu capture of the current kernel at
     # this workload (profiles/launches_bench_mixed_gauss_d10.md); None elsewhere.
-    traffic = 107.07e9 if (tensor_contraction and args.workload == "mixed" and not args.n) else None
+    traffic = 117.33e9 if (tensor_contraction and args.workload == "mixed" and not args.n) else None
 
     solve = None
     if not args.no_solve and rank == 0:

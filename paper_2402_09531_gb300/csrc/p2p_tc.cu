@@ -14,18 +14,19 @@
 // N=16, adds E_lo*q_hi: three terms (~2^-20 relative each) in two MMAs per
 // K step.  Each source block accumulates into a 32-column TMEM tile (FP32),
 // whose two halves are read back, added and folded into Kahan-compensated
-// running sums.
+// running sums kept in shared memory.
 //
-// One CTA = 128 targets, warp-specialised: eight compute warps (warps w and
-// w+4 share the TMEM lanes of quadrant w, each evaluating half of every
-// 32-source chunk), one warp whose lane 0 issues the MMAs and one whose
-// lane 0 issues the TMA loads.  The roles hand over through mbarriers only
-// (stage full / coordinates free / charges free, A full / A empty, D full /
-// D empty), so the compute warps never wait at a CTA-wide barrier inside the
-// loop; every waiting thread sleeps in the barrier (mbarrier.try_wait with
-// a suspend-time hint) until the phase completes.  TMEM: two A buffers
-// (2 x 64 columns: 32 sources hi + lo) and two 32-column accumulators, 256
-// columns allocated.  Every wait is bounded.
+// One CTA = 128 targets, warp-specialised: twelve compute warps (warps w,
+// w+4 and w+8 share the TMEM lanes of quadrant w, each evaluating a third
+// of every 48-source chunk, 8 sources per call), one warp whose lane 0
+// issues the MMAs and one whose lane 0 issues the TMA loads.  The roles hand
+// over through mbarriers only (stage full / coordinates free / charges free,
+// A full / A empty, D full / D empty), so the compute warps never wait at a
+// CTA-wide barrier inside the loop; every waiting thread sleeps in the
+// barrier (mbarrier.try_wait with a suspend-time hint) until the phase
+// completes.  TMEM: two A buffers (2 x 96 columns: 48 sources hi + lo) and
+// two 32-column accumulators, 256 columns allocated.  72 registers per
+// thread, two CTAs per SM.  Every wait is bounded.
 #include <cstdint>
 
 #include "dwfmm_internal.cuh"
@@ -37,9 +38,10 @@ namespace {
 
 using namespace tc;
 
-constexpr int kCompWarps = 8;
+constexpr int kCompWarps = 12;
+constexpr int kFoldWarps = 8;                        // parts 0 and 1 of each quadrant fold the sums
 constexpr int kTcThreads = (kCompWarps + 2) * 32;   // compute warps, MMA warp, TMA warp
-constexpr int kChunkS = 32;                          // sources per A buffer
+constexpr int kChunkS = 48;                          // sources per A buffer
 constexpr int kTmemCols = 256;
 constexpr int kRow = 256;                // shared-memory row stride (floats) of the coordinates
 
@@ -194,7 +196,7 @@ __global__ void __launch_bounds__(kTcThreads, (D <= 12 ? 2 : 1)) k_sum_tc(TcArgs
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sptr(&afull[i])), "r"(kCompWarps));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sptr(&aempty[i])));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sptr(&dfull[i])));
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sptr(&dempty[i])), "r"(kCompWarps));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sptr(&dempty[i])), "r"(kFoldWarps));
     }
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sptr(fin)));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -278,7 +280,7 @@ __global__ void __launch_bounds__(kTcThreads, (D <= 12 ? 2 : 1)) k_sum_tc(TcArgs
             break;
           }
           const uint32_t bq_addr = sptr(stage0 + st * stage_bytes + coord_pad);
-          const uint32_t d_tmem = tmem + 128 + 32 * db;
+          const uint32_t d_tmem = tmem + 192 + 32 * db;
           for (int c0 = 0; c0 < s8; c0 += kChunkS) {
             const int ab = chunk & 1;
             if (!wait_sleep(&afull[ab], static_cast<uint32_t>((chunk >> 1) & 1))) {
@@ -287,14 +289,14 @@ __global__ void __launch_bounds__(kTcThreads, (D <= 12 ? 2 : 1)) k_sum_tc(TcArgs
             }
             asm volatile("tcgen05.fence::after_thread_sync;");
             const int ns = min(kChunkS, s8 - c0);
-            const uint32_t a_tmem = tmem + 64 * ab;
+            const uint32_t a_tmem = tmem + 96 * ab;
             for (int ks = 0; ks < ns; ks += 8) {
               const uint32_t boff = static_cast<uint32_t>(((c0 + ks) / 4) * 128);
               // rows 0..15 of B = q_hi, rows 16..31 = q_lo (the lo block
               // starts 16 * ld floats = two 8-row groups after the hi block)
               const u64 bq = smem_desc(bq_addr + boff, 128, static_cast<uint32_t>(ld * 32));
               mma_tf32(d_tmem, a_tmem + ks, bq, kIdesc32, (c0 + ks) > 0 ? 1u : 0u);
-              mma_tf32(d_tmem, a_tmem + 32 + ks, bq, kIdesc16, 1u);
+              mma_tf32(d_tmem, a_tmem + kChunkS + ks, bq, kIdesc16, 1u);
             }
             mma_commit(&aempty[ab]);
             ++chunk;
@@ -311,7 +313,7 @@ __global__ void __launch_bounds__(kTcThreads, (D <= 12 ? 2 : 1)) k_sum_tc(TcArgs
     }
   } else {
     // ---- compute warps: E for (quadrant targets) x (half of each chunk)
-    const int qd = warp & 3, hf = warp >> 2;
+    const int qd = warp & 3, hf = warp >> 2;   // hf: part 0..2 of each chunk
     const uint32_t lane_base = tmem + (static_cast<uint32_t>(qd * 32) << 16);
     const int ti = half * 128 + qd * 32 + lane;
     const int tsafe = ti < ld ? ti : 0;
@@ -324,15 +326,20 @@ __global__ void __launch_bounds__(kTcThreads, (D <= 12 ? 2 : 1)) k_sum_tc(TcArgs
     }
     // target factor of the factored Gaussian
     const float tfac = (KER == DWFMM_K_GAUSS) ? exp2f(-tp[D * ld]) : 1.0f;
-    float acc[8], comp[8];
+    // Kahan sums in shared memory: [16 RHS][128 targets], values then compensations
+    float* ksum = reinterpret_cast<float*>(stage0 + 2 * stage_bytes);
+    const int trow = qd * 32 + lane;
+    if (hf < 2) {
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      acc[r] = 0.0f;
-      comp[r] = 0.0f;
+      for (int r = 0; r < 8; ++r) {
+        ksum[(8 * hf + r) * 128 + trow] = 0.0f;
+        ksum[2048 + (8 * hf + r) * 128 + trow] = 0.0f;
+      }
     }
     bool bad = false;
     // fold accumulator k (this warp's 8 right-hand sides) into the sums
     auto fold = [&](int k) {
+      if (hf >= 2) return;
       const int db = k & 1;
       const bool ok = wait_sleep(&dfull[db], static_cast<uint32_t>((k >> 1) & 1));
       if (__any_sync(0xffffffffu, !ok)) {
@@ -341,13 +348,15 @@ __global__ void __launch_bounds__(kTcThreads, (D <= 12 ? 2 : 1)) k_sum_tc(TcArgs
       }
       asm volatile("tcgen05.fence::after_thread_sync;");
       uint32_t dv[8], dl[8];
-      tmem_ld8x2(lane_base + 128 + 32 * db + 8 * hf, lane_base + 128 + 32 * db + 16 + 8 * hf, dv, dl);
+      tmem_ld8x2(lane_base + 192 + 32 * db + 8 * hf, lane_base + 192 + 32 * db + 16 + 8 * hf, dv, dl);
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
-        const float y = (__uint_as_float(dv[r]) + __uint_as_float(dl[r])) - comp[r];
-        const float s = acc[r] + y;
-        comp[r] = (s - acc[r]) - y;
-        acc[r] = s;
+        float* pa = ksum + (8 * hf + r) * 128 + trow;
+        const float acc = pa[0], comp = pa[2048];
+        const float y = (__uint_as_float(dv[r]) + __uint_as_float(dl[r])) - comp;
+        const float s = acc + y;
+        pa[2048] = (s - acc) - y;
+        pa[0] = s;
       }
       asm volatile("tcgen05.fence::before_thread_sync;");
       __syncwarp();
@@ -373,18 +382,18 @@ __global__ void __launch_bounds__(kTcThreads, (D <= 12 ? 2 : 1)) k_sum_tc(TcArgs
         asm volatile("tcgen05.fence::after_thread_sync;");
         const int j0 = c0 + 16 * hf;
         const int jn = min(16, s8 - j0);
-        const uint32_t col = static_cast<uint32_t>(64 * ab + 16 * hf);
-        if (jn >= 16) {
-          uint32_t hi[16], lo[16];
-          eval8<D, KER>(sc, j0, xt2, hi, lo);
-          eval8<D, KER>(sc, j0 + 8, xt2, hi + 8, lo + 8);
-          tmem_st16(lane_base + col, hi);
-          tmem_st16(lane_base + col + 32, lo);
-        } else if (jn > 0) {
+        const uint32_t col = static_cast<uint32_t>(96 * ab + 16 * hf);
+        if (jn > 0) {
           uint32_t hi[8], lo[8];
           eval8<D, KER>(sc, j0, xt2, hi, lo);
           tmem_st8(lane_base + col, hi);
-          tmem_st8(lane_base + col + 32, lo);
+          tmem_st8(lane_base + col + kChunkS, lo);
+        }
+        if (jn > 8) {
+          uint32_t hi[8], lo[8];
+          eval8<D, KER>(sc, j0 + 8, xt2, hi, lo);
+          tmem_st8(lane_base + col + 8, hi);
+          tmem_st8(lane_base + col + kChunkS + 8, lo);
         }
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;");
@@ -405,11 +414,13 @@ __global__ void __launch_bounds__(kTcThreads, (D <= 12 ? 2 : 1)) k_sum_tc(TcArgs
     }
     if (!bad && kb >= 1) fold(kb - 1);
     if (bad && lane == 0) atomicExch(a.err, 3);
-    if (ti < ld) {
+    if (ti < ld && hf < 2) {
       float* op = a.out + g * a.out_gstride + ti;
 #pragma unroll
-      for (int r = 0; r < 8; ++r)
-        if (8 * hf + r < a.Rc) op[(8 * hf + r) * ld] = (KER == DWFMM_K_GAUSS) ? acc[r] * tfac : acc[r];
+      for (int r = 0; r < 8; ++r) {
+        const float v = ksum[(8 * hf + r) * 128 + trow];
+        if (8 * hf + r < a.Rc) op[(8 * hf + r) * ld] = (KER == DWFMM_K_GAUSS) ? v * tfac : v;
+      }
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -423,7 +434,7 @@ __global__ void __launch_bounds__(kTcThreads, (D <= 12 ? 2 : 1)) k_sum_tc(TcArgs
 // tcgen05.alloc never has to wait for columns.
 size_t tc_smem(int D, int ld) {
   const size_t pad = static_cast<size_t>((D + 1) * kRow * 4);
-  const size_t need = 2 * (pad + static_cast<size_t>(2 * 16 * ld * 4)) + 1024;
+  const size_t need = 2 * (pad + static_cast<size_t>(2 * 16 * ld * 4)) + 1024 + 16384;   // + Kahan sums
   return need < 80 * 1024 ? 80 * 1024 : need;
 }
 
