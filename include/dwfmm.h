@@ -61,12 +61,16 @@ typedef enum {
 
 /* Arithmetic of the matvec.  FP64: every phase in float64.  FP32: near field
  * (P2P), couplings (M2L) and expansions in float32 with compensated
- * accumulation.  MIXED: FP32 with the near-field contraction (targets x
- * sources x right-hand sides) on the tensor cores when 9..16 right-hand
- * sides are passed: TF32 with a hi/lo split of both operands and three
- * products (~2^-20 relative per term), FP32 accumulation, compensated
- * fold per source block.  CG dot products and vectors are float64 in every
- * mode. */
+ * accumulation.  MIXED: FP32 with the near-field and M2L contractions
+ * (targets x sources x right-hand sides) on the tensor cores when 9..16
+ * right-hand sides are passed: TF32 with a hi/lo split of both operands and
+ * three products (~2^-20 relative per term), FP32 accumulation, compensated
+ * fold per source block.  The Gaussian takes that path in factored form
+ * (exp(-|x-y|^2/(2 sigma^2)) as a product of per-site factors and
+ * 2^(2 x'.y')) when |x|^2 log2(e) / (2 sigma^2) <= 30 over the sites'
+ * bounding box, and the float32 CUDA-core path otherwise; results agree
+ * to float32 accuracy either way.  CG dot products and vectors are float64
+ * in every mode. */
 typedef enum {
   DWFMM_P_FP64 = 0,
   DWFMM_P_FP32 = 1,
