@@ -65,6 +65,15 @@ void Plan::free_tree() {
   bq32.release();
   bqm32.release();
   near_parts64.release();
+  sym_t.release();
+  sym_s.release();
+  sym_uprow.release();
+  sym_lorow.release();
+  sym_loslot.release();
+  sym_pf.release();
+  sym_pt.release();
+  sym_nup = 0;
+  sym_ok = false;
   dpad = -1;
 }
 
@@ -264,6 +273,7 @@ dwfmm_status dwfmm_tree_build(dwfmm_plan plan, const double* pts, int64_t n, int
     dw::build_tree(P, dev, n, ld);
     dw::build_lists(P);
     dw::build_cluster_data(P);
+    dw::build_sym_lists(P);
     // bound of |x'|^2 = |x|^2 log2(e) / (2 sigma^2) over the root box, which
     // holds every site and every interpolation node
     P.gauss_fact = false;

@@ -278,6 +278,13 @@ struct Plan {
   DBuf<float> bq32;           // TF32 hi/lo charge blocks for the tensor-core P2P
   DBuf<float> bqm32;          // the same for the tensor-core M2L (moments at the nodes)
   DBuf<double> near_parts64;  // partial near-field sums of small float64 problems (split lists)
+  // symmetric float64 near field: upper entries (T, S >= T) of the near list,
+  // per-leaf rows of the upper and lower lists, slots of the lower entries,
+  // forward and transposed partial sums
+  DBuf<int32_t> sym_t, sym_s, sym_uprow, sym_lorow, sym_loslot;
+  DBuf<double> sym_pf, sym_pt;
+  int64_t sym_nup = 0;
+  bool sym_ok = false;
   cudaEvent_t ev_scaled = nullptr;
   DBuf<int> d_err;   // device error flag (3 = a bounded wait timed out)
 
@@ -312,6 +319,7 @@ void launch_scatter(Plan& P, double* y, int64_t ldy, int r0, int Rc, bool fp64);
 void launch_farfield(Plan& P, int Rc, bool fp64);
 void launch_m2l(Plan& P, int Rc, bool fp64);
 void launch_nearfield(Plan& P, int Rc, bool fp64, cudaStream_t s);
+void build_sym_lists(Plan& P);              // upper / lower near lists (symmetric float64 P2P)
 bool p2p_f32_tuned(Plan& P, int Rc, cudaStream_t s);
 bool m2l_f32_tuned(Plan& P, int Rc);
 void check_device_error(Plan& P);

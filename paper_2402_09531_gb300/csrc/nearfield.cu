@@ -8,8 +8,18 @@
 // One CTA per target group, one thread per target, sources staged through
 // shared memory in chunks.  This generic kernel serves float64 (parity) and
 // the fallback float32 shapes; the tuned float32 P2P lives in p2p_f32.cu.
+//
+// The float64 P2P has a symmetric form as well: phi is symmetric and so is
+// the near relation, so each unordered pair of near leaves (T, S) is
+// evaluated once and contributes to both y_T (with x_S) and y_S (with x_T).
+// One CTA per entry (T, S >= T) of the upper near list writes a forward
+// partial (sums over S for the targets of T) and, off the diagonal, a
+// transposed partial (sums over T for the sources of S: warp butterflies,
+// then the four warps in order); a second kernel adds each leaf's partials
+// in list order, so the result is deterministic.
 #include <algorithm>
 #include <type_traits>
+#include <vector>
 
 #include "dwfmm_internal.cuh"
 
@@ -217,7 +227,237 @@ void p2p_impl(Plan& P, int Rc, const T* pts, const T* xb, T* ynear, cudaStream_t
                                                      o_gstride, P.m_pad, Rc, reinterpret_cast<double*>(ynear));
 }
 
+// ---- symmetric float64 near field -------------------------------------
+
+constexpr int kSymMaxRc = 4;
+
+// Per row T of the near list: entries with S >= T (upper) and S < T (lower).
+__global__ void k_sym_count(const int32_t* rowptr, const int32_t* col, int L, int* nup, int* nlo) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= L) return;
+  int u = 0, l = 0;
+  for (int e = rowptr[t]; e < rowptr[t + 1]; ++e) (col[e] >= t ? u : l) += 1;
+  nup[t] = u;
+  nlo[t] = l;
+}
+
+__global__ void k_sym_fill(const int32_t* rowptr, const int32_t* col, int L, const int32_t* uprow,
+                           const int32_t* lorow, int32_t* up_t, int32_t* up_s, int32_t* lo_src) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= L) return;
+  int u = uprow[t], l = lorow[t];
+  for (int e = rowptr[t]; e < rowptr[t + 1]; ++e) {
+    const int s = col[e];
+    if (s >= t) {
+      up_t[u] = t;
+      up_s[u] = s;
+      ++u;
+    } else {
+      lo_src[l++] = s;
+    }
+  }
+}
+
+// Slot of the lower entry (X, T < X): the position of (T, X) in the upper
+// list; a missing one means the near relation is not symmetric.
+__global__ void k_sym_slots(const int32_t* lorow, const int32_t* lo_src, const int32_t* uprow, const int32_t* up_s,
+                            int L, int32_t* lo_slot, int* bad) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= L) return;
+  for (int k = lorow[x]; k < lorow[x + 1]; ++k) {
+    const int t = lo_src[k];
+    int slot = -1;
+    for (int e = uprow[t]; e < uprow[t + 1]; ++e)
+      if (up_s[e] == x) {
+        slot = e;
+        break;
+      }
+    if (slot < 0) atomicExch(bad, 1);
+    lo_slot[k] = slot < 0 ? 0 : slot;
+  }
+}
+
+// One CTA per upper entry e = (T, S): forward sums pf[e][r][i] over the
+// sources of S for target i of T; for S != T also pt[e][r][j] = sum over
+// the targets of T of phi * x_T for source j of S.  Leaves hold <= 128
+// points (one target per thread).
+template <int KER, int DM, int RC>
+__global__ void __launch_bounds__(kThreads)
+k_near_sym(const int32_t* up_t, const int32_t* up_s, int d, double inv_sigma, const double* pts, int64_t gstride,
+           int ld, const int32_t* count, int count_off, const double* xb, int64_t q_gstride, int Rc, double* pf,
+           double* pt) {
+  __shared__ double sc[DM * kSrcChunk];
+  __shared__ double sqs[RC * kSrcChunk];
+  __shared__ double zw[4 * RC * kSrcChunk];
+  const int64_t e = blockIdx.x;
+  const int T = up_t[e], S = up_s[e];
+  const int tcnt = count[count_off + T], scnt = count[count_off + S];
+  const int i = threadIdx.x, warp = i >> 5, lane = i & 31;
+  double xt[DM], qt[RC], acc[RC];
+#pragma unroll
+  for (int k = 0; k < DM; ++k) xt[k] = (k < d && i < tcnt) ? pts[T * gstride + static_cast<int64_t>(k) * ld + i] : 0.0;
+#pragma unroll
+  for (int r = 0; r < RC; ++r) {
+    qt[r] = (r < Rc && i < tcnt) ? xb[T * q_gstride + static_cast<int64_t>(r) * ld + i] : 0.0;
+    acc[r] = 0.0;
+  }
+  const bool transposed = S != T;
+  for (int cb = 0; cb < scnt; cb += kSrcChunk) {
+    const int cn = min(kSrcChunk, scnt - cb);
+    __syncthreads();
+    for (int idx = i; idx < DM * kSrcChunk; idx += kThreads) {
+      const int k = idx / kSrcChunk, j = idx % kSrcChunk;
+      sc[idx] = (j < cn && k < d) ? pts[S * gstride + static_cast<int64_t>(k) * ld + cb + j] : 0.0;
+    }
+    for (int idx = i; idx < RC * kSrcChunk; idx += kThreads) {
+      const int r = idx / kSrcChunk, j = idx % kSrcChunk;
+      sqs[idx] = (j < cn && r < Rc) ? xb[S * q_gstride + static_cast<int64_t>(r) * ld + cb + j] : 0.0;
+    }
+    __syncthreads();
+    for (int j = 0; j < cn; ++j) {
+      double r2 = 0.0;
+#pragma unroll
+      for (int k = 0; k < DM; ++k) {
+        const double df = xt[k] - sc[k * kSrcChunk + j];
+        r2 += df * df;
+      }
+      const double ph = phi_r2<double, KER>(r2, inv_sigma);
+#pragma unroll
+      for (int r = 0; r < RC; ++r) acc[r] += ph * sqs[r * kSrcChunk + j];
+      if (transposed) {
+#pragma unroll
+        for (int r = 0; r < RC; ++r) {
+          double v = ph * qt[r];
+#pragma unroll
+          for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+          if (lane == 0) zw[(warp * RC + r) * kSrcChunk + j] = v;
+        }
+      }
+    }
+    if (transposed) {
+      __syncthreads();
+      if (i < cn) {
+#pragma unroll
+        for (int r = 0; r < RC; ++r) {
+          if (r >= Rc) break;
+          const double v = ((zw[(0 * RC + r) * kSrcChunk + i] + zw[(1 * RC + r) * kSrcChunk + i]) +
+                            zw[(2 * RC + r) * kSrcChunk + i]) +
+                           zw[(3 * RC + r) * kSrcChunk + i];
+          pt[(e * Rc + r) * ld + cb + i] = v;
+        }
+      }
+    }
+  }
+  if (transposed) {   // sources of the padding: zero, so the sum over partials may run to ld
+    for (int j = scnt + i; j < ld; j += kThreads)
+      for (int r = 0; r < Rc; ++r) pt[(e * Rc + r) * ld + j] = 0.0;
+  }
+  if (i < ld) {
+#pragma unroll
+    for (int r = 0; r < RC; ++r)
+      if (r < Rc) pf[(e * Rc + r) * ld + i] = acc[r];
+  }
+}
+
+// y[X][r][i] = sum of X's forward partials, then of the transposed partials
+// of its lower entries, each in list order.
+__global__ void k_sym_reduce(const int32_t* uprow, const int32_t* lorow, const int32_t* lo_slot, int L, int ld,
+                             int Rc, const double* pf, const double* pt, double* y, int64_t o_gstride) {
+  const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= static_cast<int64_t>(L) * Rc * ld) return;
+  const int i = static_cast<int>(t % ld);
+  const int r = static_cast<int>((t / ld) % Rc);
+  const int x = static_cast<int>(t / (static_cast<int64_t>(ld) * Rc));
+  double acc = 0.0;
+  for (int e = uprow[x]; e < uprow[x + 1]; ++e) acc += pf[(static_cast<int64_t>(e) * Rc + r) * ld + i];
+  for (int k = lorow[x]; k < lorow[x + 1]; ++k) acc += pt[(static_cast<int64_t>(lo_slot[k]) * Rc + r) * ld + i];
+  y[x * o_gstride + static_cast<int64_t>(r) * ld + i] = acc;
+}
+
+template <int KER, int DM>
+void launch_near_sym_rc(Plan& P, int Rc, cudaStream_t s) {
+  const int64_t gs = static_cast<int64_t>(P.d) * P.m_pad;
+  const int64_t qg = static_cast<int64_t>(kRC) * P.m_pad;
+#define DW_SYM(RCV)                                                                                                k_near_sym<KER, DM, RCV><<<static_cast<unsigned>(P.sym_nup), kThreads, 0, s>>>(                                      P.sym_t.p, P.sym_s.p, P.d, 1.0 / P.sigma, P.d_pts64.p, gs, P.m_pad, P.d_count.p, P.L - 1, P.xb64.p, qg, Rc,       P.sym_pf.p, P.sym_pt.p)
+  if (Rc <= 1) DW_SYM(1);
+  else DW_SYM(kSymMaxRc);
+#undef DW_SYM
+}
+
+template <int KER>
+void launch_near_sym_k(Plan& P, int Rc, cudaStream_t s) {
+  if (P.d <= 4) launch_near_sym_rc<KER, 4>(P, Rc, s);
+  else if (P.d <= 8) launch_near_sym_rc<KER, 8>(P, Rc, s);
+  else if (P.d <= 12) launch_near_sym_rc<KER, 12>(P, Rc, s);
+  else if (P.d <= 16) launch_near_sym_rc<KER, 16>(P, Rc, s);
+  else launch_near_sym_rc<KER, 20>(P, Rc, s);
+}
+
+bool near_sym(Plan& P, int Rc, cudaStream_t s) {
+  if (!P.sym_ok || Rc > kSymMaxRc || P.m_pad > kThreads || P.d > 20 || P.sym_nup <= 0) return false;
+  const size_t per = static_cast<size_t>(P.sym_nup) * Rc * P.m_pad;
+  P.sym_pf.alloc(per);
+  P.sym_pt.alloc(per);
+  switch (P.kernel) {
+    case DWFMM_K_EXP: launch_near_sym_k<DWFMM_K_EXP>(P, Rc, s); break;
+    case DWFMM_K_MATERN32: launch_near_sym_k<DWFMM_K_MATERN32>(P, Rc, s); break;
+    default: launch_near_sym_k<DWFMM_K_GAUSS>(P, Rc, s);
+  }
+  const int64_t n = static_cast<int64_t>(P.L) * Rc * P.m_pad;
+  k_sym_reduce<<<ceil_div(n, 256), 256, 0, s>>>(P.sym_uprow.p, P.sym_lorow.p, P.sym_loslot.p, P.L, P.m_pad, Rc,
+                                                 P.sym_pf.p, P.sym_pt.p, P.ynear64.p,
+                                                 static_cast<int64_t>(kRC) * P.m_pad);
+  return true;
+}
+
 }  // namespace
+
+// Upper / lower near lists of the symmetric float64 near field (tree build).
+void build_sym_lists(Plan& P) {
+  P.sym_ok = false;
+  P.sym_nup = 0;
+  const int L = P.L;
+  if (P.N == 0 || L <= 0 || P.nnear <= 0) return;
+  cudaStream_t s = P.stream;
+  DBuf<int> cu, cl, bad;
+  cu.alloc(L);
+  cl.alloc(L);
+  bad.alloc(1);
+  DW_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), s));
+  k_sym_count<<<ceil_div(L, 128), 128, 0, s>>>(P.d_near_rowptr.p, P.d_near_col.p, L, cu.p, cl.p);
+  std::vector<int> hu(L), hl(L);
+  DW_CUDA(cudaMemcpyAsync(hu.data(), cu.p, sizeof(int) * L, cudaMemcpyDeviceToHost, s));
+  DW_CUDA(cudaMemcpyAsync(hl.data(), cl.p, sizeof(int) * L, cudaMemcpyDeviceToHost, s));
+  DW_CUDA(cudaStreamSynchronize(s));
+  std::vector<int32_t> up(L + 1, 0), lo(L + 1, 0);
+  for (int t = 0; t < L; ++t) {
+    up[t + 1] = up[t] + hu[t];
+    lo[t + 1] = lo[t] + hl[t];
+  }
+  const int64_t nup = up[L], nlo = lo[L];
+  // a symmetric relation with every leaf near itself has nup = nlo + L
+  if (nup != nlo + L) return;
+  P.sym_uprow.alloc(L + 1);
+  P.sym_lorow.alloc(L + 1);
+  P.sym_t.alloc(static_cast<size_t>(nup));
+  P.sym_s.alloc(static_cast<size_t>(nup));
+  P.sym_loslot.alloc(static_cast<size_t>(std::max<int64_t>(nlo, 1)));
+  DBuf<int32_t> lo_src;
+  lo_src.alloc(static_cast<size_t>(std::max<int64_t>(nlo, 1)));
+  DW_CUDA(cudaMemcpyAsync(P.sym_uprow.p, up.data(), sizeof(int32_t) * (L + 1), cudaMemcpyHostToDevice, s));
+  DW_CUDA(cudaMemcpyAsync(P.sym_lorow.p, lo.data(), sizeof(int32_t) * (L + 1), cudaMemcpyHostToDevice, s));
+  k_sym_fill<<<ceil_div(L, 128), 128, 0, s>>>(P.d_near_rowptr.p, P.d_near_col.p, L, P.sym_uprow.p, P.sym_lorow.p,
+                                             P.sym_t.p, P.sym_s.p, lo_src.p);
+  k_sym_slots<<<ceil_div(L, 128), 128, 0, s>>>(P.sym_lorow.p, lo_src.p, P.sym_uprow.p, P.sym_s.p, L, P.sym_loslot.p,
+                                              bad.p);
+  int hbad = 0;
+  DW_CUDA(cudaMemcpyAsync(&hbad, bad.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  DW_CUDA(cudaStreamSynchronize(s));
+  DW_CUDA(cudaGetLastError());
+  if (hbad) return;
+  P.sym_nup = nup;
+  P.sym_ok = true;
+}
 
 // Every target block against every source leaf in float64 (exact evaluation).
 void eval_f64(Plan& P, const double* tgt64, int G, const int32_t* rowptr, const int32_t* col, int Rc, double* out,
@@ -238,7 +478,9 @@ void launch_m2l(Plan& P, int Rc, bool fp64) {
 }
 
 void launch_nearfield(Plan& P, int Rc, bool fp64, cudaStream_t s) {
-  if (fp64) p2p_impl<double>(P, Rc, P.d_pts64.p, P.xb64.p, P.ynear64.p, s);
+  if (fp64) {
+    if (!near_sym(P, Rc, s)) p2p_impl<double>(P, Rc, P.d_pts64.p, P.xb64.p, P.ynear64.p, s);
+  }
   else if (!p2p_f32_tuned(P, Rc, s)) p2p_impl<float>(P, Rc, P.d_pts32.p, P.xb32.p, P.ynear32.p, s);
   DW_CUDA(cudaGetLastError());
 }
