@@ -393,9 +393,14 @@ void launch_near_sym_k(Plan& P, int Rc, cudaStream_t s) {
   else launch_near_sym_rc<KER, 20>(P, Rc, s);
 }
 
+// Partial sums of the symmetric form: 2 x upper entries x RHS x leaf doubles;
+// above this the list kernel runs instead.
+constexpr size_t kSymMaxBytes = size_t(8) << 30;
+
 bool near_sym(Plan& P, int Rc, cudaStream_t s) {
   if (!P.sym_ok || Rc > kSymMaxRc || P.m_pad > kThreads || P.d > 20 || P.sym_nup <= 0) return false;
   const size_t per = static_cast<size_t>(P.sym_nup) * Rc * P.m_pad;
+  if (2 * per * sizeof(double) > kSymMaxBytes) return false;
   P.sym_pf.alloc(per);
   P.sym_pt.alloc(per);
   switch (P.kernel) {
