@@ -115,6 +115,48 @@ def _ptr(a) -> int | None:
     return a.ctypes.data
 
 
+def _ld(a, name: str) -> int:
+    """Row stride (in elements) of a 2-D float64 array whose rows are
+    contiguous: the layout every buffer of the C ABI has.  Anything else
+    (another dtype, a strided column, fewer than two dimensions) would be
+    misread on the C side, so it raises ValueError here."""
+    if hasattr(a, "data_ptr"):
+        import torch
+        if a.dtype != torch.float64:
+            raise ValueError(f"{name} must be float64, got {a.dtype}")
+        if a.dim() != 2:
+            raise ValueError(f"{name} must be 2-D, got shape {tuple(a.shape)}")
+        rows, cols = int(a.shape[0]), int(a.shape[1])
+        if cols > 1 and a.stride(1) != 1:
+            raise ValueError(f"{name} must have contiguous rows (column stride 1)")
+        ld = int(a.stride(0))
+    else:
+        if a.dtype != np.float64:
+            raise ValueError(f"{name} must be float64, got {a.dtype}")
+        if a.ndim != 2:
+            raise ValueError(f"{name} must be 2-D, got shape {a.shape}")
+        rows, cols = int(a.shape[0]), int(a.shape[1])
+        if cols > 1 and a.strides[1] != 8:
+            raise ValueError(f"{name} must have contiguous rows (column stride 8 bytes)")
+        if a.strides[0] % 8 != 0:
+            raise ValueError(f"{name} row stride must be a multiple of 8 bytes")
+        ld = int(a.strides[0] // 8)
+    if rows > 1 and ld < cols:
+        raise ValueError(f"{name} rows overlap (row stride {ld} < {cols} columns)")
+    return max(ld, cols) if rows <= 1 else ld
+
+
+def _same_layout(ref, ref_name: str, ld: int, *others):
+    """Buffers that the C ABI reads with one row stride must share it."""
+    for a, name in others:
+        if a is None:
+            continue
+        if tuple(a.shape) != tuple(ref.shape):
+            raise ValueError(f"{name} must have the shape of {ref_name} {tuple(ref.shape)}, got {tuple(a.shape)}")
+        if _ld(a, name) != ld:
+            raise ValueError(f"{name} must have the row stride of {ref_name} ({ld})")
+
+
 def _stream_handle(stream) -> int | None:
     if stream is None:
         try:
@@ -166,6 +208,12 @@ class Plan:
         except Exception:
             pass
 
+    def _cols(self, a, name: str):
+        """Once a tree is built, (R, N) buffers must have N columns."""
+        n = getattr(self, "n", None)
+        if n is not None and int(a.shape[1]) != n:
+            raise ValueError(f"{name} must have N = {n} columns, got {int(a.shape[1])}")
+
     def check(self, st: int):
         if st != OK:
             msg = self._l.dwfmm_last_error(self.h).decode() if self.h else ""
@@ -179,23 +227,29 @@ class Plan:
     def tree_build(self, pts, stream=None):
         """pts: (N, d) float64, torch (cuda or cpu) or numpy, row-major."""
         n = int(pts.shape[0])
-        ld = int(pts.stride(0)) if hasattr(pts, "stride") and callable(pts.stride) else \
-            int(pts.strides[0] // 8) if n else self.d
+        ld = _ld(pts, "pts") if n else self.d
+        if n and int(pts.shape[1]) != self.d:
+            raise ValueError(f"pts must have d = {self.d} columns, got {int(pts.shape[1])}")
         self._pts_keep = pts
+        self.n = None   # no tree until the build succeeds
         self.check(self._l.dwfmm_tree_build(self.h, _ptr(pts), n, ld, _stream_handle(stream)))
         self.n = n
 
     def matvec(self, x, y, stream=None):
         """x, y: (R, N) float64 (each row one right-hand side, contiguous)."""
         R = int(x.shape[0])
-        ldx = int(x.stride(0)) if hasattr(x, "stride") and callable(x.stride) else int(x.strides[0] // 8)
-        ldy = int(y.stride(0)) if hasattr(y, "stride") and callable(y.stride) else int(y.strides[0] // 8)
+        ldx, ldy = _ld(x, "x"), _ld(y, "y")
+        self._cols(x, "x")
+        if tuple(y.shape) != tuple(x.shape):
+            raise ValueError(f"y must have the shape of x {tuple(x.shape)}, got {tuple(y.shape)}")
         self.check(self._l.dwfmm_matvec(self.h, _ptr(x), _ptr(y), R, ldx, ldy, _stream_handle(stream)))
         return y
 
     def solve(self, lam: float, f, c, rtol: float = 1e-6, maxit: int = 1000, stream=None):
         R = int(f.shape[0])
-        ld = int(f.stride(0)) if hasattr(f, "stride") and callable(f.stride) else int(f.strides[0] // 8)
+        ld = _ld(f, "f")
+        self._cols(f, "f")
+        _same_layout(f, "f", ld, (c, "c"))
         it = C.c_int32(0)
         rel = (C.c_double * R)()
         st = self._l.dwfmm_solve(self.h, float(lam), _ptr(f), _ptr(c), R, ld, float(rtol), int(maxit),
@@ -205,11 +259,14 @@ class Plan:
     def evaluate(self, targets, c, out, stream=None):
         """Interpolant at new points: out (R, nt) = sum_j phi(|t - x_j|) c (R, N)."""
         nt = int(targets.shape[0])
-        ldt = int(targets.stride(0)) if hasattr(targets, "stride") and callable(targets.stride) else \
-            int(targets.strides[0] // 8)
+        ldt = _ld(targets, "targets") if nt else self.d
         R = int(c.shape[0])
-        ldc = int(c.stride(0)) if hasattr(c, "stride") and callable(c.stride) else int(c.strides[0] // 8)
-        ldo = int(out.stride(0)) if hasattr(out, "stride") and callable(out.stride) else int(out.strides[0] // 8)
+        ldc, ldo = _ld(c, "c"), _ld(out, "out")
+        self._cols(c, "c")
+        if nt and int(targets.shape[1]) != self.d:
+            raise ValueError(f"targets must have d = {self.d} columns, got {int(targets.shape[1])}")
+        if tuple(out.shape) != (R, nt):
+            raise ValueError(f"out must have shape {(R, nt)}, got {tuple(out.shape)}")
         self.check(self._l.dwfmm_evaluate(self.h, _ptr(targets), nt, ldt, _ptr(c), ldc, _ptr(out), ldo, R,
                                           _stream_handle(stream)))
         return out
@@ -217,9 +274,11 @@ class Plan:
     # -- incremental CG (many solves in flight) -----------------------------
     def cg_begin(self, lam: float, f, rtol: float = 1e-6, stream=None):
         """f: (R, N) float64 cuda tensor."""
+        ld = _ld(f, "f")
+        self._cols(f, "f")
         self._cg_R = int(f.shape[0])
         self._cg_f = f
-        self.check(self._l.dwfmm_cg_begin(self.h, float(lam), _ptr(f), self._cg_R, int(f.stride(0)),
+        self.check(self._l.dwfmm_cg_begin(self.h, float(lam), _ptr(f), self._cg_R, ld,
                                           float(rtol), _stream_handle(stream)))
 
     def cg_step(self, iters: int, stream=None):
@@ -236,13 +295,16 @@ class Plan:
         return bool(ready.value), st, it, rr
 
     def cg_result(self, c, stream=None):
-        self.check(self._l.dwfmm_cg_result(self.h, _ptr(c), int(c.stride(0)) if hasattr(c, "stride") and
-                                           callable(c.stride) else int(c.strides[0] // 8), _stream_handle(stream)))
+        ld = _ld(c, "c")
+        self._cols(c, "c")
+        self.check(self._l.dwfmm_cg_result(self.h, _ptr(c), ld, _stream_handle(stream)))
         return c
 
     def residual(self, lam: float, f, c, r=None, stream=None):
         R = int(f.shape[0])
-        ld = int(f.stride(0)) if hasattr(f, "stride") and callable(f.stride) else int(f.strides[0] // 8)
+        ld = _ld(f, "f")
+        self._cols(f, "f")
+        _same_layout(f, "f", ld, (c, "c"), (r, "r"))
         rel = np.zeros(R)
         self.check(self._l.dwfmm_residual(self.h, float(lam), _ptr(f), _ptr(c), _ptr(r), R, ld,
                                           rel.ctypes.data, _stream_handle(stream)))
@@ -254,7 +316,9 @@ class Plan:
         else the minimal-residual length); r must hold f - (K64 + lam I) c.
         c and r are updated in place.  Returns (alpha, relres)."""
         R = int(f.shape[0])
-        ld = int(f.stride(0)) if hasattr(f, "stride") and callable(f.stride) else int(f.strides[0] // 8)
+        ld = _ld(f, "f")
+        self._cols(f, "f")
+        _same_layout(f, "f", ld, (c, "c"), (delta, "delta"), (r, "r"))
         alpha = np.zeros(R)
         rel = np.zeros(R)
         self.check(self._l.dwfmm_refine(self.h, float(lam), _ptr(f), _ptr(c), _ptr(delta), _ptr(r), R, ld,
@@ -324,6 +388,13 @@ class Batch:
 
     def matvec(self, xs, ys, stream=None):
         """xs[i], ys[i]: (nrhs_i, N_i) float64 cuda tensors (contiguous)."""
+        if len(xs) != len(self.plans) or len(ys) != len(self.plans):
+            raise ValueError(f"one x and one y per problem ({len(self.plans)})")
+        for i, (x, y) in enumerate(zip(xs, ys)):
+            want = (self.nrhs[i], int(getattr(self.plans[i], "n", -1)))
+            for a, name in ((x, f"xs[{i}]"), (y, f"ys[{i}]")):
+                if _ld(a, name) != want[1] or tuple(a.shape) != want:
+                    raise ValueError(f"{name} must be a contiguous {want} float64 tensor, got {tuple(a.shape)}")
         xp = (C.c_void_p * len(xs))(*[x.data_ptr() for x in xs])
         yp = (C.c_void_p * len(ys))(*[y.data_ptr() for y in ys])
         st = self._l.dwfmm_batch_matvec(self.h, xp, yp, _stream_handle(stream))

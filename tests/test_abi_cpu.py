@@ -84,3 +84,27 @@ def test_binding_fails_loudly_without_library(tmp_path):
     from paper_2402_09531_gb300 import dwfmm
     with pytest.raises(ImportError):
         dwfmm.load(str(tmp_path / "missing.so"))
+
+
+def test_binding_rejects_buffers_the_abi_would_misread():
+    """Every (R, N) / (N, d) buffer crosses the C ABI as a pointer plus a row
+    stride of float64 elements; the binding refuses any other layout before
+    a call is made."""
+    import torch
+    from paper_2402_09531_gb300.dwfmm import _ld, _same_layout
+    assert _ld(np.zeros((3, 10)), "a") == 10
+    assert _ld(np.zeros((4, 12))[:, :10], "a") == 12
+    assert _ld(torch.zeros((2, 7), dtype=torch.float64), "t") == 7
+    assert _ld(torch.zeros((1, 0), dtype=torch.float64), "t") >= 0
+    bad = [np.zeros((3, 10), dtype=np.float32), np.zeros(10), np.zeros((10, 3)).T,
+           torch.zeros((2, 3)), torch.zeros((3, 2), dtype=torch.float64).t(),
+           torch.zeros(5, dtype=torch.float64)]
+    for b in bad:
+        with pytest.raises(ValueError):
+            _ld(b, "b")
+    f = np.zeros((2, 5))
+    _same_layout(f, "f", 5, (np.zeros((2, 5)), "c"), (None, "r"))
+    with pytest.raises(ValueError):
+        _same_layout(f, "f", 5, (np.zeros((2, 6))[:, :5], "c"))
+    with pytest.raises(ValueError):
+        _same_layout(f, "f", 5, (np.zeros((3, 5)), "c"))
