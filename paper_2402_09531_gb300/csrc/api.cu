@@ -264,13 +264,17 @@ dwfmm_status dwfmm_tree_build(dwfmm_plan plan, const double* pts, int64_t n, int
     P.cgs.drop_graph();
     ++P.tree_gen;
     const double* dev = pts;
+    int64_t ld_dev = ld;
     dw::DBuf<double> staged;
     if (n > 0 && !is_device_pointer(pts)) {
-      staged.alloc(static_cast<size_t>(n) * ld);
-      DW_CUDA(cudaMemcpyAsync(staged.p, pts, sizeof(double) * n * ld, cudaMemcpyHostToDevice, P.stream));
+      // the d used columns of each row only (a host buffer may end right after them)
+      staged.alloc(static_cast<size_t>(n) * P.d);
+      DW_CUDA(cudaMemcpy2DAsync(staged.p, sizeof(double) * P.d, pts, sizeof(double) * ld, sizeof(double) * P.d, n,
+                                cudaMemcpyHostToDevice, P.stream));
       dev = staged.p;
+      ld_dev = P.d;
     }
-    dw::build_tree(P, dev, n, ld);
+    dw::build_tree(P, dev, n, ld_dev);
     dw::build_lists(P);
     dw::build_cluster_data(P);
     dw::build_sym_lists(P);
@@ -639,9 +643,12 @@ dwfmm_status dwfmm_evaluate(dwfmm_plan plan, const double* targets, int64_t nt, 
     double* od = out;
     int64_t lt = ld_t, lc = ld_c, lo = ld_o;
     if (!is_device_pointer(targets)) {
-      ts.alloc(static_cast<size_t>(nt) * ld_t);
-      DW_CUDA(cudaMemcpyAsync(ts.p, targets, sizeof(double) * nt * ld_t, cudaMemcpyHostToDevice, P.stream));
+      // the d used columns of each row only (a host buffer may end right after them)
+      ts.alloc(static_cast<size_t>(nt) * P.d);
+      DW_CUDA(cudaMemcpy2DAsync(ts.p, sizeof(double) * P.d, targets, sizeof(double) * ld_t, sizeof(double) * P.d, nt,
+                                cudaMemcpyHostToDevice, P.stream));
       td = ts.p;
+      lt = P.d;
     }
     if (!is_device_pointer(c)) {
       cs.alloc(static_cast<size_t>(P.N) * nrhs);
