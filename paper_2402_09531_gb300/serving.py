@@ -70,7 +70,10 @@ def estimate_bytes(n: int, d: int, nrhs: int, leaf: int, n_x: int) -> int:
     per_site = d * 8 * 6 + 16 * 4 * 8 + 16 * 8 * 4 + nrhs * 8 * 8 + 64
     per_cluster = n_pad * 16 * 4 * 8 + n_pad * (d + 1) * 12 + d * 8 * 6
     near_pairs = leaves * 64
-    return int(n * per_site + clusters * per_cluster + near_pairs * 24 + (32 << 20))
+    # partial sums of the symmetric float64 near field (also run by the
+    # float64 residuals of float32 / mixed plans): 2 x upper entries x RHS x leaf
+    sym_partials = near_pairs * nrhs * leaf * 8
+    return int(n * per_site + clusters * per_cluster + near_pairs * 24 + sym_partials + (32 << 20))
 
 
 @dataclass
