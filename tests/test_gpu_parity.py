@@ -207,6 +207,32 @@ def test_fp64_paper_weight_rule():
     assert o.rel_err(y, o.fmm_matvec(pb, f)) <= FP64_TOL
 
 
+@pytest.mark.parametrize("leaf,nrhs", [(128, 4), (256, 2), (128, 5)])
+def test_fp64_symmetric_near_field_limits(leaf, nrhs):
+    """The float64 near field evaluates each unordered near pair once when
+    leaves hold <= 128 points and there are <= 4 right-hand sides (leaf 128
+    with 4 RHS: both limits), and runs the list kernel otherwise (leaf 256;
+    5 RHS).  Both match the oracle, and repeated matvecs are bit-identical
+    (the partial sums are added in a fixed order)."""
+    torch = _torch()
+    w = di.Workload(f"sym_{leaf}_{nrhs}", d=3, n=2600, gamma=np.array([1.0, 0.5, 0.25]), kernel="matern32",
+                    q=4.0, leaf=leaf, eta=1.0, nrhs=nrhs, seed=61)
+    X, f = di.sites_and_rhs(w)
+    pb = o.make_problem(X, w.kernel, o.weights_inv_gamma(w.gamma), w.q, w.leaf, w.eta)
+    plan = _plan(w, "fp64", max_rhs=nrhs)
+    plan.set_nodes(pb.exp_.nodes)
+    plan.tree_build(torch.from_numpy(X).cuda())
+    xd = torch.from_numpy(f).cuda()
+    y1 = torch.full_like(xd, float("nan"))
+    y2 = torch.full_like(xd, float("nan"))
+    plan.matvec(xd, y1)
+    plan.matvec(xd, y2)
+    torch.cuda.synchronize()
+    assert o.rel_err(y1.cpu().numpy(), o.fmm_matvec(pb, f)) <= FP64_TOL
+    assert torch.equal(y1, y2)
+    plan.close()
+
+
 def test_host_buffers_match_device_buffers():
     w, X, f, pb = _case("small", 2000, seed=6, nrhs=2)
     _, yh = _gpu_matvec(w, X, f, pb, "fp64", host=True)
