@@ -319,6 +319,9 @@ void launch_scatter(Plan& P, double* y, int64_t ldy, int r0, int Rc, bool fp64);
 void launch_farfield(Plan& P, int Rc, bool fp64);
 void launch_m2l(Plan& P, int Rc, bool fp64);
 void launch_nearfield(Plan& P, int Rc, bool fp64, cudaStream_t s);
+// Bit of the current device in a per-device mask (kernel attributes are set
+// per device); devices beyond 63 get no bit, so their setup simply repeats.
+uint64_t device_bit();
 void build_sym_lists(Plan& P);              // upper / lower near lists (symmetric float64 P2P)
 bool p2p_f32_tuned(Plan& P, int Rc, cudaStream_t s);
 bool m2l_f32_tuned(Plan& P, int Rc);

@@ -191,13 +191,15 @@ __global__ void k_sum_parts(const double* part, int splits, int64_t stride, int6
 }
 
 int sm_count() {
-  static int n = 0;
-  if (n == 0) {
-    int dev = 0;
-    DW_CUDA(cudaGetDevice(&dev));
-    DW_CUDA(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+  static int n[64] = {0};
+  int dev = 0;
+  DW_CUDA(cudaGetDevice(&dev));
+  int v = dev < 64 ? n[dev] : 0;
+  if (v == 0) {
+    DW_CUDA(cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev));
+    if (dev < 64) n[dev] = v;
   }
-  return n;
+  return v;
 }
 
 template <typename T>
@@ -416,6 +418,12 @@ bool near_sym(Plan& P, int Rc, cudaStream_t s) {
 }
 
 }  // namespace
+
+uint64_t device_bit() {
+  int dev = 0;
+  DW_CUDA(cudaGetDevice(&dev));
+  return dev < 64 ? (uint64_t(1) << dev) : 0;
+}
 
 // Upper / lower near lists of the symmetric float64 near field (tree build).
 void build_sym_lists(Plan& P) {

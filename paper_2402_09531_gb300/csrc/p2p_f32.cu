@@ -423,10 +423,11 @@ void dispatch(int D, int kernel, int RC, SumArgs a, int groups, int threads, siz
   }
 }
 
-bool g_attrs_done = false;
+uint64_t g_attrs_dev = 0;   // devices whose kernel attributes are set
 
 void ensure_attrs() {
-  if (g_attrs_done) return;
+  const uint64_t bit = device_bit();
+  if (g_attrs_dev & bit) return;
   set_attrs<4>();
   set_attrs<8>();
   set_attrs<10>();
@@ -434,7 +435,7 @@ void ensure_attrs() {
   set_attrs<16>();
   set_attrs<20>();
   DW_CUDA(cudaGetLastError());
-  g_attrs_done = true;
+  g_attrs_dev |= bit;
 }
 
 // Scaled blocks for the current tree: leaf sites and cluster nodes.

@@ -455,7 +455,7 @@ void tc_attrs_d() {
   cudaFuncSetAttribute(k_sum_tc<D, DWFMM_K_GAUSS>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
 }
 
-bool g_tc_attrs = false;
+uint64_t g_tc_attrs_dev = 0;   // devices whose kernel attributes are set
 
 }  // namespace
 
@@ -474,7 +474,8 @@ bool sum_tc(int D, int kernel, const float* tgt, int64_t tgt_gstride, const floa
   if (gauss && !gauss_factored) return false;
   const size_t smem = tc_smem(D, ld);
   if (smem > 200 * 1024) return false;
-  if (!g_tc_attrs) {
+  const uint64_t dbit = device_bit();
+  if (!(g_tc_attrs_dev & dbit)) {
     tc_attrs_d<4>();
     tc_attrs_d<8>();
     tc_attrs_d<10>();
@@ -482,7 +483,7 @@ bool sum_tc(int D, int kernel, const float* tgt, int64_t tgt_gstride, const floa
     tc_attrs_d<16>();
     tc_attrs_d<20>();
     DW_CUDA(cudaGetLastError());
-    g_tc_attrs = true;
+    g_tc_attrs_dev |= dbit;
   }
   bq_scratch.alloc(static_cast<size_t>(groups_src) * 2 * 16 * ld);
   const int64_t nq = groups_src * ld * 16;
