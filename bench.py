@@ -171,6 +171,23 @@ def finish_oracle_subprocess(p, timeout: float = 600.0):
 # our arm
 # ---------------------------------------------------------------------------
 
+def max_over_ranks(dist, device, x: float) -> float:
+    """The largest value over the ranks (the slowest replica bounds the job);
+    x itself on a single process."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, n: int, nrhs: int, seconds_per_step: float) -> float:
+    """Whole-job points x RHS per second: every rank processes its own
+    replica of N x R per step, and the step takes the slowest rank's time."""
+    return world * n * nrhs / seconds_per_step
+
+
 def near_pairs(plan) -> int:
     import numpy as np
     t = plan.export_tree()
@@ -258,12 +275,9 @@ def run_ours(args):
     plan.set_profiling(False)
     ms = statistics.mean(step_ms)
     total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(dist, dev, total_ms)
     ms_max = total_ms / args.steps
-    value = world * N * R / (ms_max / 1e3)
+    value = job_throughput(world, N, R, ms_max / 1e3)
 
     # e2e through the public API with host buffers (pinned), copies inside
     xh = torch.from_numpy(f).pin_memory()
@@ -278,11 +292,7 @@ def run_ours(args):
             t0 = time.perf_counter()
             plan.matvec(xh, yh)               # synchronises (host y)
             e2e_s.append(time.perf_counter() - t0)
-    e2e_t = statistics.mean(e2e_s)
-    if dist:
-        t = torch.tensor([e2e_t], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_t = float(t.item())
+    e2e_t = max_over_ranks(dist, dev, statistics.mean(e2e_s))
 
     # roofline of the dominant kernel (P2P): algorithmic FP32 flops per launch.
     # MIXED plans with 9..16 RHS contract on the tensor cores (k_sum_tc): the
@@ -348,7 +358,7 @@ def run_ours(args):
                        "depth": depth, "far_blocks": n_far, "near_blocks": n_near, "near_pairs": pairs,
                        "precision": args.precision, "parallelism": f"replicas x{world}",
                        "l2": "flushed between steps (512 MiB write)"},
-            "e2e": {"value": world * N * R / e2e_t, "unit": UNIT, "h2d_bytes_per_step": int(xh.numel() * 8),
+            "e2e": {"value": job_throughput(world, N, R, e2e_t), "unit": UNIT, "h2d_bytes_per_step": int(xh.numel() * 8),
                     "d2h_bytes_per_step": int(yh.numel() * 8)},
             "gpu_launches": int(launches),
             "roofline": {"kernel": ("p2p (near field): k_sum_tc, kernel evaluation on the FP32 pipe, "
