@@ -280,6 +280,12 @@ def test_lists_partition_matrix_exactly_once():
     fs = {tuple(p) for lvl in ls.far for p in lvl}
     assert fs == {(s, t) for (t, s) in fs}
     assert {tuple(p) for p in ls.near} == {(s, t) for (t, s) in ls.near}
+    # every leaf is near itself (a cluster is never admissible with itself):
+    # with the symmetry above, the upper entries (t, s >= t) number
+    # (|near| + leaves) / 2, which the symmetric float64 near field relies on
+    leaves = set(range(*tr.level_range(tr.depth)))
+    assert all((t, t) in {tuple(p) for p in ls.near} for t in leaves)
+    assert sum(1 for (t, s) in ls.near if s >= t) * 2 == len(ls.near) + len(leaves)
 
 
 def test_far_pairs_admissible_parents_not_by_euclid():
