@@ -119,6 +119,46 @@ def test_rho_identity_and_normalisation():
     np.testing.assert_allclose(o.weights_inv_gamma([0.5, 0.25, 0.125]), [1, 2, 4])
 
 
+def _golden_weights():
+    rows = []
+    with open(os.path.join(GOLDEN, "sec6_2_weights.txt")) as fh:
+        for line in fh:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            kind, rest = line.split(None, 1)
+            rows.append((kind, rest))
+    return rows
+
+
+def test_weights_match_hand_worked_values():
+    """Sec. 6.2 rule and the unnormalised omega_k = log rho_k of Theorem 4.6
+    against values worked by hand from the surds rho(tau) (golden file)."""
+    rows = _golden_weights()
+    assert sum(k == "paper" for k, _ in rows) == 2 and sum(k == "logrho" for k, _ in rows) == 2
+    for kind, rest in rows:
+        if kind == "paper":
+            lhs, rhs = rest.split(";")
+            eta, *b = [float(v) for v in lhs.split()]
+            want = np.array([float(v) for v in rhs.split()])
+            np.testing.assert_allclose(o.weights_paper_normalised(np.array(b), eta), want, rtol=0, atol=2e-15)
+        else:
+            tau, want = [float(v) for v in rest.split()]
+            np.testing.assert_allclose(o.weights_log_rho(np.array([tau])), [want], rtol=0, atol=2e-15)
+
+
+def test_planted_inverted_tau_is_caught(monkeypatch):
+    """tau_k = eta / b_k instead of 1 / (eta b_k) keeps omega_1 = 1 and the
+    monotone order, but not the hand-worked values."""
+    def bad(b, eta):
+        b = np.asarray(b, dtype=np.float64)
+        tau = eta / b
+        return np.log(math.e * o.rho_of_tau(tau) / o.rho_of_tau(tau[0]))
+    monkeypatch.setattr(o, "weights_paper_normalised", bad)
+    with pytest.raises(AssertionError):
+        test_weights_match_hand_worked_values()
+
+
 # --------------------------------------------------------------------------
 # Legendre basis (Sec. 5.2)
 # --------------------------------------------------------------------------
