@@ -326,22 +326,26 @@ dwfmm_status dwfmm_phase_times(dwfmm_plan plan, double* ms, int64_t* launches, i
  * has no counterpart of this entry point; it reuses the library's float32
  * near-field kernel on blocks of 256 sites.
  *
- * pts, x, y: device pointers (float64).  pts is N x d row-major (leading
- * dimension ld_pts >= d); x and y are column-major N x nrhs (leading
- * dimensions ldx, ldy >= N).  Limits: N <= 8192, 1 <= d <= 16,
- * 1 <= nrhs <= 16; larger sizes return DWFMM_ERR_INVALID_ARG.  The result is
- * float32-accurate (relative error ~1e-7); a bounded shared-memory wait that
- * gave up writes NaN into y.
+ * pts, x, y: device pointers (float64) of the current device (or managed
+ * memory); unlike dwfmm_matvec this entry point does not stage host
+ * buffers, and a host pointer returns DWFMM_ERR_INVALID_ARG.  pts is N x d
+ * row-major (leading dimension ld_pts >= d); x and y are column-major
+ * N x nrhs (leading dimensions ldx, ldy >= N).  Limits: N <= 8192,
+ * 1 <= d <= 16, 1 <= nrhs <= 16; larger sizes return DWFMM_ERR_INVALID_ARG.
+ * The result is float32-accurate (relative error ~1e-7); a bounded
+ * shared-memory wait that gave up writes NaN into y.
  *
  * All intermediates live in one fixed device array of about 1.6 MB inside
  * the library, which every GPU that loads the library keeps until the
- * process exits.  The first call on each device looks up that array's
- * device address and sets kernel attributes (no allocation); make that
- * first call before any stream capture.  The array is shared by all calls on
- * a device and keeps the last call's contents; each call rewrites what it
- * reads, so calls ordered on one stream are safe, but calls whose work
- * overlaps on the GPU (e.g. on unsynchronised streams) race on it.
- * Work is enqueued on `stream`; the call does not synchronise. */
+ * process exits.  The first call on each device sets kernel attributes and
+ * looks up that array's device address (no allocation); make that first
+ * call before any stream capture: a first call made while `stream` is
+ * capturing returns DWFMM_ERR_STATE.  Later calls outside capture look the
+ * address up again.  The array is shared by all calls on a device and keeps
+ * the last call's contents; each call rewrites what it reads, so calls
+ * ordered on one stream are safe, but calls whose work overlaps on the GPU
+ * (e.g. on unsynchronised streams) race on it.  Work is enqueued on
+ * `stream`; the call does not synchronise. */
 dwfmm_status dwfmm_direct_sum_noalloc(int32_t kernel, double sigma, const double* pts, int64_t n,
                                       int32_t d, int64_t ld_pts, const double* x, double* y,
                                       int32_t nrhs, int64_t ldx, int64_t ldy, void* stream);

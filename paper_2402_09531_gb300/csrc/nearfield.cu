@@ -18,6 +18,7 @@
 // then the four warps in order); a second kernel adds each leaf's partials
 // in list order, so the result is deterministic.
 #include <algorithm>
+#include <atomic>
 #include <type_traits>
 #include <vector>
 
@@ -191,13 +192,13 @@ __global__ void k_sum_parts(const double* part, int splits, int64_t stride, int6
 }
 
 int sm_count() {
-  static int n[64] = {0};
+  static std::atomic<int> n[64];   // per device; 0 = not looked up yet
   int dev = 0;
   DW_CUDA(cudaGetDevice(&dev));
-  int v = dev < 64 ? n[dev] : 0;
+  int v = dev < 64 ? n[dev].load() : 0;
   if (v == 0) {
     DW_CUDA(cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev));
-    if (dev < 64) n[dev] = v;
+    if (dev < 64) n[dev].store(v);
   }
   return v;
 }

@@ -20,7 +20,9 @@
 //  - Per source block the contributions are summed in float32 partials, then
 //    folded into per-target running sums with Kahan compensation (kept in
 //    shared memory).
+#include <atomic>
 #include <cstdint>
+#include <string>
 
 #include "dwfmm_internal.cuh"
 
@@ -423,11 +425,14 @@ void dispatch(int D, int kernel, int RC, SumArgs a, int groups, int threads, siz
   }
 }
 
-uint64_t g_attrs_dev = 0;   // devices whose kernel attributes are set
+// Devices whose kernel attributes are set.  Atomic: host threads may make
+// their first call on a device at the same time (both then set the same
+// attributes, which is harmless).
+std::atomic<uint64_t> g_attrs_dev{0};
 
 void ensure_attrs() {
   const uint64_t bit = device_bit();
-  if (g_attrs_dev & bit) return;
+  if (g_attrs_dev.load() & bit) return;
   set_attrs<4>();
   set_attrs<8>();
   set_attrs<10>();
@@ -435,7 +440,7 @@ void ensure_attrs() {
   set_attrs<16>();
   set_attrs<20>();
   DW_CUDA(cudaGetLastError());
-  g_attrs_dev |= bit;
+  g_attrs_dev.fetch_or(bit);
 }
 
 // Scaled blocks for the current tree: leaf sites and cluster nodes.
@@ -709,20 +714,45 @@ __global__ void k_na_finish(NaLayout l, int64_t n, int R, double* y, int64_t ldy
   y[r * ldy + i] = (*l.err) ? __longlong_as_double(0x7ff8000000000000ll) : v;
 }
 
-// Device address of the scratch array, looked up once per device.
+// Device address of the scratch array.  Outside stream capture it is looked
+// up on every call (cudaGetSymbolAddress allocates nothing), so a context
+// that was reset still gets the right address; the last address seen per
+// device serves calls made during capture, where the first call on a device
+// must not load the module or set kernel attributes.
 constexpr int kNaMaxDevices = 64;
-float* g_na_ptr[kNaMaxDevices] = {nullptr};
+std::atomic<float*> g_na_ptr[kNaMaxDevices];
 
-float* na_scratch_for_current_device() {
+float* na_scratch_for_current_device(cudaStream_t s) {
   int dev = 0;
   DW_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kNaMaxDevices) fail(DWFMM_ERR_INVALID_ARG, "device index out of range");
-  if (!g_na_ptr[dev]) {
-    void* p = nullptr;
-    DW_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-    g_na_ptr[dev] = static_cast<float*>(p);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  DW_CUDA(cudaStreamIsCapturing(s, &cap));
+  if (cap != cudaStreamCaptureStatusNone) {
+    float* p = g_na_ptr[dev].load();
+    if (!p)
+      fail(DWFMM_ERR_STATE,
+           "direct_sum_noalloc: the first call on a device sets it up and must come before any stream capture");
+    return p;
   }
-  return g_na_ptr[dev];
+  ensure_attrs();
+  void* p = nullptr;
+  DW_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+  g_na_ptr[dev].store(static_cast<float*>(p));
+  return static_cast<float*>(p);
+}
+
+// Buffers the kernels read or write directly: device (or managed) memory of
+// the current device.  A host pointer would fault on the GPU.
+void na_check_device_buffer(const void* p, int dev, const char* name) {
+  cudaPointerAttributes a;
+  const cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) (void)cudaGetLastError();
+  const bool ok = e == cudaSuccess &&
+                  ((a.type == cudaMemoryTypeDevice && a.device == dev) || a.type == cudaMemoryTypeManaged);
+  if (!ok)
+    fail(DWFMM_ERR_INVALID_ARG, std::string("direct_sum_noalloc: ") + name +
+                                    " must be device memory of the current device");
 }
 
 }  // namespace
@@ -736,11 +766,15 @@ dwfmm_status direct_sum_noalloc(int kernel, double sigma, const double* pts, int
   if (n == 0) return DWFMM_OK;
   if (!pts || !x || !y || ldp < d || ldx < n || ldy < n)
     fail(DWFMM_ERR_INVALID_ARG, "direct_sum_noalloc: NULL buffer or leading dimension too small");
+  int dev = 0;
+  DW_CUDA(cudaGetDevice(&dev));
+  na_check_device_buffer(pts, dev, "pts");
+  na_check_device_buffer(x, dev, "x");
+  na_check_device_buffer(y, dev, "y");
   const int D = padded_dim(d);
   const int RC = padded_rc(R);
   const int G = static_cast<int>((n + kNaBlock - 1) / kNaBlock);
-  ensure_attrs();
-  const NaLayout l = na_layout(na_scratch_for_current_device());
+  const NaLayout l = na_layout(na_scratch_for_current_device(s));
   k_na_prepare<<<ceil_div(static_cast<int64_t>(G) * kNaBlock + G * G, 256), 256, 0, s>>>(
       pts, n, d, ldp, D, kernel, sigma, x, R, RC, ldx, l, G);
   SumArgs a{};

@@ -12,9 +12,12 @@
 // and staged by TMA bulk copies.  The hi and lo charge blocks are adjacent
 // in that layout, so one N=32 product gives E_hi*[q_hi | q_lo] and a second,
 // N=16, adds E_lo*q_hi: three terms (~2^-20 relative each) in two MMAs per
-// K step.  Each source block accumulates into a 32-column TMEM tile (FP32),
-// whose two halves are read back, added and folded into Kahan-compensated
-// running sums kept in shared memory.
+// K step.  Each source block accumulates into a 32-column TMEM tile (FP32):
+// columns 0..15 hold E_hi*q_hi, columns 16..31 the two small terms.  The
+// tensor core rounds its accumulator toward zero at every MMA, a bias that
+// grows with the number of updates, so the large terms get one update per
+// K step and the small ones the other.  The two halves are read back, added
+// and folded into Kahan-compensated running sums kept in shared memory.
 //
 // One CTA = 128 targets, warp-specialised: twelve compute warps (warps w,
 // w+4 and w+8 share the TMEM lanes of quadrant w, each evaluating a third
@@ -27,6 +30,7 @@
 // completes.  TMEM: two A buffers (2 x 96 columns: 48 sources hi + lo) and
 // two 32-column accumulators, 256 columns allocated.  72 registers per
 // thread, two CTAs per SM.  Every wait is bounded.
+#include <atomic>
 #include <cstdint>
 
 #include "dwfmm_internal.cuh"
@@ -296,7 +300,10 @@ __global__ void __launch_bounds__(kTcThreads, (D <= 12 ? 2 : 1)) k_sum_tc(TcArgs
               // starts 16 * ld floats = two 8-row groups after the hi block)
               const u64 bq = smem_desc(bq_addr + boff, 128, static_cast<uint32_t>(ld * 32));
               mma_tf32(d_tmem, a_tmem + ks, bq, kIdesc32, (c0 + ks) > 0 ? 1u : 0u);
-              mma_tf32(d_tmem, a_tmem + kChunkS + ks, bq, kIdesc16, 1u);
+              // the small term E_lo*q_hi joins E_hi*q_lo in columns 16..31:
+              // the tensor core truncates its FP32 accumulator at every
+              // MMA, so the large E_hi*q_hi columns take one update per step
+              mma_tf32(d_tmem + 16, a_tmem + kChunkS + ks, bq, kIdesc16, 1u);
             }
             mma_commit(&aempty[ab]);
             ++chunk;
@@ -455,7 +462,7 @@ void tc_attrs_d() {
   cudaFuncSetAttribute(k_sum_tc<D, DWFMM_K_GAUSS>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
 }
 
-uint64_t g_tc_attrs_dev = 0;   // devices whose kernel attributes are set
+std::atomic<uint64_t> g_tc_attrs_dev{0};   // devices whose kernel attributes are set
 
 }  // namespace
 
@@ -475,7 +482,7 @@ bool sum_tc(int D, int kernel, const float* tgt, int64_t tgt_gstride, const floa
   const size_t smem = tc_smem(D, ld);
   if (smem > 200 * 1024) return false;
   const uint64_t dbit = device_bit();
-  if (!(g_tc_attrs_dev & dbit)) {
+  if (!(g_tc_attrs_dev.load() & dbit)) {
     tc_attrs_d<4>();
     tc_attrs_d<8>();
     tc_attrs_d<10>();
@@ -483,7 +490,7 @@ bool sum_tc(int D, int kernel, const float* tgt, int64_t tgt_gstride, const floa
     tc_attrs_d<16>();
     tc_attrs_d<20>();
     DW_CUDA(cudaGetLastError());
-    g_tc_attrs_dev |= dbit;
+    g_tc_attrs_dev.fetch_or(dbit);
   }
   bq_scratch.alloc(static_cast<size_t>(groups_src) * 2 * 16 * ld);
   const int64_t nq = groups_src * ld * 16;

@@ -1,22 +1,22 @@
-"""The allocation-free direct sum against the library's own exact path.
+"""The allocation-free direct sum against the float64 oracle's dense product.
 
-dwfmm_direct_sum_noalloc serves callers that cannot call cudaMalloc (their
-framework owns the device memory pool, or their loop cannot take the device
-synchronisation that allocation implies); it keeps all intermediates in a
-fixed array inside the library.  Its result must match what dwfmm_matvec
-gives for the same sites when the whole set fits in one leaf (then the FMM
-has no far field and is the exact direct sum), within the float32 tolerance
-used by the other float32 tests, on two calls in a row (the second call
-reuses the array the first one left behind).
+dwfmm_direct_sum_noalloc serves callers that cannot call cudaMalloc: a host
+application whose framework owns the device memory pool (its caching
+allocator has reserved nearly all of it), or a loop that cannot take the
+device synchronisation that allocation implies.  It keeps all
+intermediates in a fixed array inside the library.  Its result must match
+the exact y = K x of the oracle's brute-force product within the float32
+tolerance of the other float32 tests, on two calls in a row (the second
+call reuses the array the first one left behind), up to the array's
+limits (N = 8192, d = 16, 16 right-hand sides), for every kernel.
 
 This file is named so that pytest collects it last.
 """
-import ctypes as C
-
 import numpy as np
 import pytest
 
 import dwfmm_inputs as di
+from oracle import dwfmm_oracle as o
 
 pytestmark = pytest.mark.gpu
 
@@ -29,20 +29,6 @@ def lib():
     ge.build()
     import paper_2402_09531_gb300 as pkg
     return pkg.lib()
-
-
-def _reference(w, X, f):
-    import torch
-    from paper_2402_09531_gb300 import Plan
-    plan = Plan(d=w.d, kernel=w.kernel, sigma=w.sigma, gamma=w.gamma, q=w.q, eta=w.eta,
-                leaf_size=1024, precision="fp32", max_rhs=f.shape[0])
-    plan.tree_build(torch.from_numpy(X).cuda())
-    assert plan.info()[3] == 0            # one leaf: the matvec is the exact sum
-    xd = torch.from_numpy(f).cuda()
-    yd = torch.empty_like(xd)
-    plan.matvec(xd, yd)
-    torch.cuda.synchronize()
-    return yd.cpu().numpy()
 
 
 def _noalloc(lib, w, X, f):
@@ -63,11 +49,24 @@ def _rel(a, b):
     return float(np.max(np.linalg.norm(a - b, axis=1) / np.linalg.norm(b, axis=1)))
 
 
-@pytest.mark.parametrize("base,n,nrhs", [("mixed", 1000, 16), ("small", 777, 3)])
-def test_noalloc_matches_single_leaf_matvec_twice(lib, base, n, nrhs):
-    w = di.scaled({"mixed": di.mixed_gauss_d10(), "small": di.small_exp_d4()}[base], n, nrhs=nrhs)
+def _case(name, n, nrhs):
+    if name == "gauss_d10":
+        return di.scaled(di.mixed_gauss_d10(), n, nrhs=nrhs)
+    if name == "exp_d4":
+        return di.scaled(di.small_exp_d4(), n, nrhs=nrhs)
+    if name == "matern_d8":
+        return di.scaled(di.fp64_matern_d8(), n, nrhs=nrhs)
+    # d = 16 (the array's largest dimension): the serving shape, exponential kernel
+    w = di.serving_requests(1)[0]
+    return di.scaled(w, n, nrhs=nrhs)
+
+
+@pytest.mark.parametrize("name,n,nrhs", [("gauss_d10", 1000, 16), ("exp_d4", 777, 3), ("matern_d8", 2049, 5),
+                                         ("exp_d16", 8192, 16)])
+def test_noalloc_matches_dense_oracle_twice(lib, name, n, nrhs):
+    w = _case(name, n, nrhs)
     X, f = di.sites_and_rhs(w)
-    ref = _reference(w, X, f)
+    ref = o.dense_matvec(w.kernel, X, f, w.sigma, chunk=256)
     first = _noalloc(lib, w, X, f)
     second = _noalloc(lib, w, X, f)
     assert np.all(np.isfinite(first)) and np.all(np.isfinite(second))
@@ -81,3 +80,27 @@ def test_noalloc_rejects_sizes_beyond_its_array(lib):
     assert st == 1
     st = lib.dwfmm_direct_sum_noalloc(pkg.KERNELS["exp"], 1.0, 1, 100, 17, 17, 1, 1, 1, 100, 100, None)
     assert st == 1
+    st = lib.dwfmm_direct_sum_noalloc(pkg.KERNELS["exp"], 1.0, 1, 100, 4, 4, 1, 1, 17, 100, 100, None)
+    assert st == 1
+
+
+def test_noalloc_rejects_host_buffers(lib):
+    """Host (numpy) buffers are refused on the host, before any kernel runs."""
+    import torch
+    import paper_2402_09531_gb300 as pkg
+    w = _case("exp_d4", 300, 2)
+    X, f = di.sites_and_rhs(w)
+    y = np.zeros_like(f)
+    Xd = torch.from_numpy(X).cuda()
+    xd = torch.from_numpy(f).cuda()
+    yd = torch.zeros_like(xd)
+    s = torch.cuda.current_stream().cuda_stream
+    k = pkg.KERNELS[w.kernel]
+    assert lib.dwfmm_direct_sum_noalloc(k, 1.0, X.ctypes.data, 300, 4, 4, xd.data_ptr(), yd.data_ptr(), 2, 300,
+                                        300, s) == 1
+    assert lib.dwfmm_direct_sum_noalloc(k, 1.0, Xd.data_ptr(), 300, 4, 4, f.ctypes.data, yd.data_ptr(), 2, 300,
+                                        300, s) == 1
+    assert lib.dwfmm_direct_sum_noalloc(k, 1.0, Xd.data_ptr(), 300, 4, 4, xd.data_ptr(), y.ctypes.data, 2, 300,
+                                        300, s) == 1
+    torch.cuda.synchronize()
+    assert np.all(y == 0.0)
