@@ -9,8 +9,8 @@ expansion setup (weights, index set, nodes, V^{-1}) and the tree build
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 --impl reference times the float64 CPU oracle on the same workload (a
-bounded sample per step: the rows of one target leaf, with the full upward
-pass).  Under torchrun each rank runs an independent replica (the method
+bounded sample per step: the rows of one target leaf per host core, each
+core with its own full upward pass).  Under torchrun each rank runs an independent replica (the method
 runs on one GPU; replicas scale weakly); rank 0 prints.
 """
 from __future__ import annotations
@@ -31,7 +31,6 @@ if ROOT not in sys.path:
 
 METRIC = "DW-FMM matvec pts·RHS/s and CG solve p50/p99 ms, mixed vs FP64 @ rel err 1e-6"
 UNIT = "pts·RHS/s"
-SMS = 152
 FP32_LANES = 128
 
 
@@ -103,45 +102,102 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-# CPU oracle sample (runs in its own single-threaded process)
+# CPU oracle sample (its own process, no GPU; one worker per host core)
 # ---------------------------------------------------------------------------
 
-def oracle_sample(name: str, steps: int, warmup: int, leaf_index: int = 0):
-    """Time the float64 oracle's matvec restricted to one target leaf (full
-    upward pass, far field of the leaf's ancestors, near field).  Tree-only
-    matrices are built before timing (they are setup, as on the GPU)."""
+def _oracle_leaves(pb, count):
+    """`count` target leaves spread evenly over the tree order."""
+    first = (1 << pb.tree.depth) - 1
+    nleaf = 1 << pb.tree.depth
+    return [first + (i * nleaf) // count for i in range(count)]
+
+
+def _ancestors(leaf):
+    anc, c = [], leaf
+    while True:
+        anc.append(c)
+        if c == 0:
+            return anc
+        c = (c - 1) // 2
+
+
+def _oracle_worker(pb, f, leaf, steps, warmup, barrier, out):
+    """One host core: the far-field coefficients of the leaf's ancestors
+    (setup), then warm-up and timed steps of the leaf-restricted matvec.
+    Every step starts at a barrier, so the workers' steps overlap."""
+    import os as _os
+    from oracle import dwfmm_oracle as o
+    t0 = time.time()
+    anc = set(_ancestors(leaf))
+    for lvl in pb.lists.far:
+        for (t, s) in lvl:
+            if int(t) in anc:
+                o.problem_coefficient(pb, int(t), int(s))
+    setup = time.time() - t0
+    times = []
+    for k in range(warmup + steps):
+        barrier.wait()
+        t = time.perf_counter()
+        o.fmm_matvec_leaves(pb, f, [leaf])
+        if k >= warmup:
+            times.append(time.perf_counter() - t)
+    out.put((leaf, setup, times, _os.getpid()))
+
+
+def cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def oracle_sample(name: str, steps: int, warmup: int, workers: int = 0):
+    """Time the float64 oracle's matvec restricted to target leaves, one leaf
+    per host core (full upward pass, far field of the leaf's ancestors, near
+    field), all cores stepping together.  The problem and the transfer
+    matrices are built once before the workers fork (setup, as on the GPU);
+    this process never touches a GPU."""
+    import multiprocessing as mp
     import numpy as np
     import dwfmm_inputs as di
     from oracle import dwfmm_oracle as o
     w = workload(name)
     X, f = di.sites_and_rhs(w)
+    W = workers or (os.cpu_count() or 1)
     t0 = time.time()
     pb = o.make_problem(X, w.kernel, o.weights_inv_gamma(w.gamma), w.q, w.leaf, w.eta, w.sigma)
-    first = (1 << pb.tree.depth) - 1
-    leaf = first + leaf_index
-    anc, c = [], leaf
-    while True:
-        anc.append(c)
-        if c == 0:
-            break
-        c = (c - 1) // 2
     for c in range(1, pb.tree.nclusters):
         o.problem_transfer(pb, c)
-    for lvl in pb.lists.far:
-        for (t, s) in lvl:
-            if int(t) in anc:
-                o.problem_coefficient(pb, int(t), int(s))
     setup_s = time.time() - t0
-    times = []
-    for k in range(warmup + steps):
-        t = time.perf_counter()
-        o.fmm_matvec_leaves(pb, f, [leaf])
-        if k >= warmup:
-            times.append(time.perf_counter() - t)
-    rows = int(pb.tree.end[leaf] - pb.tree.begin[leaf])
-    units = rows * w.nrhs
-    return {"units_per_step": units, "s_per_step": statistics.mean(times), "steps": steps,
-            "setup_s": setup_s, "rows": rows, "leaf": leaf}
+    leaves = _oracle_leaves(pb, W)
+    ctx = mp.get_context("fork")
+    barrier = ctx.Barrier(len(leaves))
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_oracle_worker, args=(pb, f, leaf, steps, warmup, barrier, q)) for leaf in leaves]
+    for p in procs:
+        p.start()
+    res = [q.get() for _ in procs]
+    for p in procs:
+        p.join()
+    step_s = [max(r[2][k] for r in res) for k in range(steps)]   # the slowest core bounds each step
+    rows = sum(int(pb.tree.end[leaf] - pb.tree.begin[leaf]) for leaf in leaves)
+    return {"units_per_step": rows * w.nrhs, "s_per_step": statistics.mean(step_s), "steps": steps,
+            "setup_s": setup_s + max(r[1] for r in res), "rows": rows, "leaves": len(leaves),
+            "cores": len(leaves), "nproc": os.cpu_count(), "cpu_model": cpu_model()}
+
+
+def oracle_sample_text(res, nrhs):
+    return (f"float64 numpy oracle, {res['leaves']} target leaves ({res['rows']} rows x {nrhs} RHS) of the "
+            f"same workload per step, one leaf per host core, all cores stepping together: each core runs "
+            f"the full upward pass, the far field of its leaf's ancestors and the near field; problem, tree, "
+            f"lists and transfer matrices built before timing ({res['setup_s']:.0f} s); mean of "
+            f"{res['steps']} steps; {res['cores']} of {res['nproc']} cores ({res['cpu_model']})")
 
 
 def start_oracle_subprocess(name: str, steps: int, warmup: int):
@@ -196,6 +252,75 @@ def near_pairs(plan) -> int:
     return int(np.sum(size[near[:, 0]] * size[near[:, 1]]))
 
 
+def kernel_source_sha(src: str) -> str:
+    import hashlib
+    with open(os.path.join(ROOT, "paper_2402_09531_gb300", "csrc", src), "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def _traffic_records():
+    """DRAM traffic per launch recorded from ncu captures, one line per
+    (kernel source, workload) in the profile summaries:
+    `traffic: <bytes> B per launch; source <file> sha16 <hash>; workload <name>`."""
+    import re
+    out = []
+    pdir = os.path.join(ROOT, "profiles")
+    pat = re.compile(r"traffic: ([0-9.eE+]+) B per launch; source (\S+) sha16 ([0-9a-f]{16}); workload (\S+)")
+    for fn in sorted(os.listdir(pdir)) if os.path.isdir(pdir) else []:
+        if not fn.endswith(".md"):
+            continue
+        with open(os.path.join(pdir, fn)) as fh:
+            for m in pat.finditer(fh.read()):
+                out.append((float(m.group(1)), m.group(2), m.group(3), m.group(4), fn))
+    return out
+
+
+def recorded_traffic(src: str, workload_name: str):
+    """The recorded traffic of this exact kernel source on this workload, else
+    None (the counters no longer describe the kernel that ran)."""
+    sha = kernel_source_sha(src)
+    for b, s_, h, wl, _ in _traffic_records():
+        if s_ == src and h == sha and wl == workload_name:
+            return b
+    return None
+
+
+def traffic_basis(src: str, workload_name: str):
+    sha = kernel_source_sha(src)
+    for b, s_, h, wl, fn in _traffic_records():
+        if s_ == src and h == sha and wl == workload_name:
+            return f"dram__bytes_read.sum + dram__bytes_write.sum of one launch (ncu, profiles/{fn})"
+    return f"none: no ncu capture of {src} at sha16 {sha} on this workload"
+
+
+def compare_fp64(plan, w, Xd, xd, yd, stream, ms_mixed):
+    """The plain float64 GPU DW-FMM on the same workload (one matvec) beside
+    the timed mixed result yd: float64 time, speed-up, and the relative
+    difference of yd, worst column and whole block."""
+    import torch
+    from paper_2402_09531_gb300 import Plan
+    p64 = Plan(d=w.d, kernel=w.kernel, sigma=w.sigma, gamma=w.gamma, q=w.q, eta=w.eta, leaf_size=w.leaf,
+               precision="fp64", max_rhs=int(xd.shape[0]))
+    p64.tree_build(Xd)
+    y64 = torch.empty_like(xd)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    p64.matvec(xd, y64)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms64 = a.elapsed_time(b)
+    diff = yd - y64
+    col = torch.linalg.norm(diff, dim=1) / torch.linalg.norm(y64, dim=1)
+    block = float(torch.linalg.norm(diff) / torch.linalg.norm(y64))
+    p64.close()
+    return {"fp64_ms_per_step": ms64, "speedup_vs_fp64": ms64 / ms_mixed,
+            "rel_diff_vs_fp64_worst_column": float(col.max()), "rel_diff_vs_fp64_block": block,
+            "rel_diff_vs_fp64_columns": [float(v) for v in col],
+            "note": "the timed mixed result against one float64 matvec of the same plan parameters and "
+                    "inputs (first float64 call, workspace allocation included)"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -209,10 +334,6 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-
-    cpu_proc = None
-    if rank == 0 and not args.no_cpu_baseline:
-        cpu_proc = start_oracle_subprocess(args.workload, args.cpu_steps, 1)
 
     import __graft_entry__ as ge
     ge.build()
@@ -305,47 +426,32 @@ def run_ours(args):
     achieved = pairs * flops_pair / (p2p_avg_ms / 1e3) / 1e12
     peaks = measured_peaks()
     clock_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    peak = SMS * FP32_LANES * 2 * clock_mhz * 1e6 / 1e12
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = sms * FP32_LANES * 2 * clock_mhz * 1e6 / 1e12
     launches = sum(v[1] for k, v in phases.items() if k != "matvec")
-    # DRAM bytes per P2P launch from a 1-pass ncu capture of the current kernel at
-    # this workload (profiles/launches_bench_mixed_gauss_d10.md); None elsewhere.
-    traffic = 117.33e9 if (tensor_contraction and args.workload == "mixed" and not args.n) else None
+    ksrc = "p2p_tc.cu" if tensor_contraction else "p2p_f32.cu"
+    traffic = recorded_traffic(ksrc, w.name) if args.precision != "fp64" else None
 
     solve = None
     if not args.no_solve and rank == 0:
         solve = run_solve_sample(args)
 
+    # CPU oracle baseline (its own process, host cores only) runs while the
+    # float64 comparison occupies the GPU
+    cpu_proc = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu_proc = start_oracle_subprocess(args.workload, args.cpu_steps, 1)
+
     fp64 = None
-    if args.compare_fp64 and rank == 0:
-        # the plain float64 GPU DW-FMM on the same workload (one step)
-        p64 = Plan(d=d, kernel=w.kernel, sigma=w.sigma, gamma=w.gamma, q=w.q, eta=w.eta, leaf_size=w.leaf,
-                   precision="fp64", max_rhs=R)
-        p64.tree_build(Xd)
-        y64 = torch.empty_like(xd)
-        p64.matvec(xd, y64)
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        p64.matvec(xd, y64)
-        b.record(stream)
-        torch.cuda.synchronize()
-        ms64 = a.elapsed_time(b)
-        plan.matvec(xd, yd)
-        torch.cuda.synchronize()
-        rel = float(torch.max(torch.linalg.norm(yd - y64, dim=1) / torch.linalg.norm(y64, dim=1)))
-        fp64 = {"fp64_ms_per_step": ms64, "speedup_vs_fp64": ms64 / ms_max, "max_rel_diff_vs_fp64": rel}
-        p64.close()
+    if not args.no_fp64 and rank == 0 and args.precision != "fp64":
+        fp64 = compare_fp64(plan, w, Xd, xd, yd, stream, ms_max)
 
     cpu = None
     if cpu_proc is not None:
         res = finish_oracle_subprocess(cpu_proc)
         if res:
-            cpu = {"value": res["units_per_step"] / res["s_per_step"], "unit": UNIT, "cores": 1,
-                   "kind": "oracle",
-                   "sample": (f"float64 numpy oracle, one target leaf ({res['rows']} rows x {R} RHS) of "
-                              f"the same workload per step: full upward pass, far field of the leaf's "
-                              f"ancestors, near field; tree-only matrices built before timing "
-                              f"({res['setup_s']:.0f} s); mean of {res['steps']} steps, 1 thread")}
+            cpu = {"value": res["units_per_step"] / res["s_per_step"], "unit": UNIT, "cores": res["cores"],
+                   "kind": "oracle", "sample": oracle_sample_text(res, R)}
 
     if rank == 0:
         line = {
@@ -370,9 +476,14 @@ def run_ours(args):
                          "tensor_flops_per_pair": (3 * 2 * 16) if tensor_contraction else 0,
                          "tensor_tflops": (pairs * 96 / (p2p_avg_ms / 1e3) / 1e12) if tensor_contraction else 0.0,
                          "launch_ms": p2p_avg_ms,
-                         "peak_basis": f"{SMS} SMs x {FP32_LANES} FP32 lanes x 2 flop x {clock_mhz:.0f} MHz"},
-            "phase_ms_per_step": {k: v[0] / args.steps for k, v in phases.items()},
+                         "traffic_basis": traffic_basis(ksrc, w.name) if args.precision != "fp64" else None,
+                         "peak_basis": f"{sms} SMs x {FP32_LANES} FP32 lanes x 2 flop x {clock_mhz:.0f} MHz "
+                                       f"(derived: no measured FP32 peak)"},
             "phase_ms_isolated": {k: v[0] / 2 for k, v in iso.items()},
+            "phase_ms_concurrent": {"note": "timed steps; the far-field phases run on the caller's stream "
+                                            "while the near field occupies the GPU from a second stream, so "
+                                            "their times include waiting for it",
+                                    **{k: v[0] / args.steps for k, v in phases.items()}},
             "setup_ms": setup_ms, "tree_build_ms": min(tree_ms),
             "clocks": clk.summary(), "clocks_e2e": clk2.summary(),
             "cpu_baseline": cpu,
@@ -482,9 +593,8 @@ def run_reference(args):
         "impl": "reference",
         "config": {"workload": w.name, "d": w.d, "N": w.n, "nrhs": w.nrhs, "kernel": w.kernel, "q": w.q,
                    "leaf": w.leaf, "eta": w.eta},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"one target leaf ({res['rows']} rows x {w.nrhs} RHS) per step, full "
-                                   f"upward pass; tree-only matrices built before timing"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": res["cores"], "kind": "oracle",
+                         "sample": oracle_sample_text(res, w.nrhs)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -501,8 +611,8 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=2)
     ap.add_argument("--n", type=int, default=0, help="override N (smaller case for profiling)")
     ap.add_argument("--no-solve", action="store_true")
-    ap.add_argument("--compare-fp64", action="store_true",
-                    help="also time one float64 matvec of the same workload (about a minute at N=2^20)")
+    ap.add_argument("--no-fp64", action="store_true",
+                    help="skip the float64 matvec of the same workload (about a minute at N=2^20)")
     ap.add_argument("--solve-requests", type=int, default=8)
     ap.add_argument("--solve-nmax", type=int, default=3000)
     ap.add_argument("--sweep-requests", type=int, default=32)

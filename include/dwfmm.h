@@ -288,6 +288,14 @@ const char* dwfmm_last_error(dwfmm_plan plan);
 dwfmm_status dwfmm_plan_info(dwfmm_plan plan, int64_t* n_x, int64_t* n_far, int64_t* n_near,
                              int32_t* depth);
 
+/* Which engine evaluated the near field N (Eq. (5.1)) in the plan's last
+ * matvec (*engine, -1 before the first): 0 float64, one CTA per target leaf
+ * over its near list; 1 float64, each unordered near pair of leaves once;
+ * 2 float32 on the CUDA cores; 3 MIXED, contraction on the tensor cores (TF32
+ * hi/lo, every ordered pair); 4 MIXED, each unordered near pair once, FP16
+ * hi/lo on the tensor cores with fixed-point transposed sums. */
+dwfmm_status dwfmm_near_engine(dwfmm_plan plan, int32_t* engine);
+
 /* Copy out plan data (host buffers, NULL to skip), for tests and tools:
  *  weights: d doubles; lam: n x d int32 multi-indices (row-major);
  *  nodes: n x d doubles; pivots: n int32 Halton indices (0-based, -1 if the

@@ -74,6 +74,11 @@ void Plan::free_tree() {
   sym_pt.release();
   sym_nup = 0;
   sym_ok = false;
+  sym_order.release();
+  sym_bq16.release();
+  sym_fwd.release();
+  sym_acc.release();
+  sym_colmax.release();
   dpad = -1;
 }
 
@@ -281,6 +286,7 @@ dwfmm_status dwfmm_tree_build(dwfmm_plan plan, const double* pts, int64_t n, int
     // bound of |x'|^2 = |x|^2 log2(e) / (2 sigma^2) over the root box, which
     // holds every site and every interpolation node
     P.gauss_fact = false;
+    P.gauss_bound = 0.0;
     if (P.kernel == DWFMM_K_GAUSS && n > 0) {
       std::vector<double> lo(P.d), hi(P.d);
       DW_CUDA(cudaMemcpyAsync(lo.data(), P.d_lo.p, sizeof(double) * P.d, cudaMemcpyDeviceToHost, P.stream));
@@ -293,6 +299,7 @@ dwfmm_status dwfmm_tree_build(dwfmm_plan plan, const double* pts, int64_t n, int
         b += m * m * s2;
       }
       P.gauss_fact = b <= 30.0;
+      P.gauss_bound = b;
     }
     P.have_tree = true;
     return DWFMM_OK;
@@ -405,6 +412,12 @@ dwfmm_status dwfmm_plan_destroy(dwfmm_plan plan) {
   if (P.side) (void)cudaStreamSynchronize(P.side);
   P.free_all();
   delete plan;
+  return DWFMM_OK;
+}
+
+dwfmm_status dwfmm_near_engine(dwfmm_plan plan, int32_t* engine) {
+  if (!plan || !engine) return DWFMM_ERR_INVALID_ARG;
+  *engine = plan->P.near_engine;
   return DWFMM_OK;
 }
 

@@ -242,6 +242,7 @@ struct Plan {
   // Gaussian kernel with every scaled squared norm |x'|^2 of the root box at
   // most 30: the tensor-core near field may evaluate it in factored form
   bool gauss_fact = false;
+  double gauss_bound = 0.0;   // that bound (Gaussian kernel)
   int64_t N = 0;
   int J = -1, L = 0, C = 0, m_pad = 0, jmin = 0;
   std::vector<int32_t> h_begin, h_count;
@@ -285,6 +286,15 @@ struct Plan {
   DBuf<double> sym_pf, sym_pt;
   int64_t sym_nup = 0;
   bool sym_ok = false;
+  // symmetric tensor-core near field (MIXED): target leaves by decreasing
+  // upper-row length, FP16 hi/lo charge blocks, forward sums, fixed-point
+  // transposed sums, per-column largest |q'| (float bits)
+  DBuf<int32_t> sym_order;
+  DBuf<uint16_t> sym_bq16;
+  DBuf<float> sym_fwd;
+  DBuf<unsigned long long> sym_acc;
+  DBuf<unsigned> sym_colmax;
+  int near_engine = -1;   // engine of the last near field (dwfmm_near_engine)
   cudaEvent_t ev_scaled = nullptr;
   DBuf<int> d_err;   // device error flag (3 = a bounded wait timed out)
 
@@ -323,6 +333,9 @@ void launch_nearfield(Plan& P, int Rc, bool fp64, cudaStream_t s);
 // per device); devices beyond 63 get no bit, so their setup simply repeats.
 uint64_t device_bit();
 void build_sym_lists(Plan& P);              // upper / lower near lists (symmetric float64 P2P)
+void sym_tc_order(Plan& P, const std::vector<int>& upper_counts);
+bool near_sym_tc(Plan& P, int D, int Rc, cudaStream_t s);   // symmetric tensor-core P2P (MIXED, 9..16 RHS)
+int sm_count();
 bool p2p_f32_tuned(Plan& P, int Rc, cudaStream_t s);
 bool m2l_f32_tuned(Plan& P, int Rc);
 void check_device_error(Plan& P);

@@ -26,6 +26,18 @@
 
 namespace dw {
 
+int sm_count() {
+  static std::atomic<int> n[64];   // per device; 0 = not looked up yet
+  int dev = 0;
+  DW_CUDA(cudaGetDevice(&dev));
+  int v = dev < 64 ? n[dev].load() : 0;
+  if (v == 0) {
+    DW_CUDA(cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev));
+    if (dev < 64) n[dev].store(v);
+  }
+  return v;
+}
+
 namespace {
 
 constexpr int kThreads = 128;
@@ -191,17 +203,6 @@ __global__ void k_sum_parts(const double* part, int splits, int64_t stride, int6
   out[t] = acc;
 }
 
-int sm_count() {
-  static std::atomic<int> n[64];   // per device; 0 = not looked up yet
-  int dev = 0;
-  DW_CUDA(cudaGetDevice(&dev));
-  int v = dev < 64 ? n[dev].load() : 0;
-  if (v == 0) {
-    DW_CUDA(cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev));
-    if (dev < 64) n[dev].store(v);
-  }
-  return v;
-}
 
 template <typename T>
 void p2p_impl(Plan& P, int Rc, const T* pts, const T* xb, T* ynear, cudaStream_t s) {
@@ -471,6 +472,7 @@ void build_sym_lists(Plan& P) {
   if (hbad) return;
   P.sym_nup = nup;
   P.sym_ok = true;
+  sym_tc_order(P, hu);
 }
 
 // Every target block against every source leaf in float64 (exact evaluation).
@@ -493,9 +495,15 @@ void launch_m2l(Plan& P, int Rc, bool fp64) {
 
 void launch_nearfield(Plan& P, int Rc, bool fp64, cudaStream_t s) {
   if (fp64) {
-    if (!near_sym(P, Rc, s)) p2p_impl<double>(P, Rc, P.d_pts64.p, P.xb64.p, P.ynear64.p, s);
+    P.near_engine = 1;
+    if (!near_sym(P, Rc, s)) {
+      P.near_engine = 0;
+      p2p_impl<double>(P, Rc, P.d_pts64.p, P.xb64.p, P.ynear64.p, s);
+    }
+  } else if (!p2p_f32_tuned(P, Rc, s)) {
+    P.near_engine = 2;
+    p2p_impl<float>(P, Rc, P.d_pts32.p, P.xb32.p, P.ynear32.p, s);
   }
-  else if (!p2p_f32_tuned(P, Rc, s)) p2p_impl<float>(P, Rc, P.d_pts32.p, P.xb32.p, P.ynear32.p, s);
   DW_CUDA(cudaGetLastError());
 }
 

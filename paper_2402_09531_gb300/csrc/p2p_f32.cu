@@ -502,13 +502,18 @@ bool p2p_f32_tuned(Plan& P, int Rc, cudaStream_t s) {
   P.xq32.alloc(static_cast<size_t>(P.L) * P.m_pad * kRC);
   const int64_t nq = static_cast<int64_t>(P.L) * P.m_pad * RC;
   k_interleave<<<ceil_div(nq, 256), 256, 0, s>>>(P.xb32.p, P.L, P.m_pad, RC, P.xq32.p);
-  // MIXED plans with 9..16 right-hand sides: contraction on the tensor cores
+  // MIXED plans with 9..16 right-hand sides: contraction on the tensor cores,
+  // each unordered near pair once where the symmetric kernel applies
+  P.near_engine = 4;
+  if (P.prec == DWFMM_P_MIXED && RC == 16 && near_sym_tc(P, D, Rc, s)) return true;
+  P.near_engine = 3;
   if (P.prec == DWFMM_P_MIXED && RC == 16 &&
       sum_tc(D, P.kernel, P.d_ptsk.p, static_cast<int64_t>(D + 1) * P.m_pad, P.d_ptsk.p,
              static_cast<int64_t>(D + 1) * P.m_pad, P.xq32.p, P.L, P.bq32, P.ynear32.p,
              static_cast<int64_t>(kRC) * P.m_pad, P.d_near_rowptr.p, P.d_near_col.p, P.d_count.p, P.L - 1, 0, 0,
              P.L, P.m_pad, Rc, P.gauss_fact, P.d_err.p, s))
     return true;
+  P.near_engine = 2;
   SumArgs a{};
   a.tgt = P.d_ptsk.p;
   a.tgt_gstride = static_cast<int64_t>(D + 1) * P.m_pad;

@@ -1,0 +1,720 @@
+// Symmetric near field (P2P) on the tensor cores for MIXED plans with 9..16
+// right-hand sides: each unordered near pair of leaves (T, S >= T) of the
+// near list N (Eq. (5.1); both orderings are in the list, K is symmetric)
+// is evaluated once and serves both directions,
+//
+//   y_T += E q_S    (forward),     y_S += E^T q_T    (transposed, S != T),
+//
+// with E[t][s] = phi(|x_t - x_s| / sigma).  For the Gaussian the factored
+// form E = 2^(-|x'|^2) 2^(2 x'.s') 2^(-|s'|^2) is used (scaled coordinates,
+// kernel constant folded in): the CUDA cores evaluate E' = 2^(2 x'.s'), the
+// point factors sit on the charges and on the finished sums.
+//
+// Arithmetic.  E' is split into FP16 hi + lo (hi = E' rounded to FP16, lo =
+// the FP16 rounding of E' - hi); the charges q' = q * factor, normalised per
+// right-hand side by a power of two so that |q'| <= 1, are split the same
+// way.  tcgen05.mma.kind::f16 (FP32 accumulation) forms hi*hi + hi*lo +
+// lo*hi, 11-bit significands on both sides like the TF32 split.  The
+// plan takes this path only where E' stays inside the FP16 range (E' <=
+// 2^15: the bound on |x'|^2 of the tree's root box) and E' <= 1 otherwise.
+//
+// Work.  One CTA per target leaf T (rows ordered by their upper-list length,
+// longest first), looping over the upper entries S >= T in 64-source
+// chunks.  Sixteen compute warps evaluate E for all targets of T (two per
+// thread: t and t + 128) against the chunk and store E_hi / E_lo into a
+// shared-memory tile in the no-swizzle core-matrix layout; one core row is
+// 8 sources of one target (16 bytes), so the same tile is
+//   * the K-major A operand of the forward product (M = 128 targets,
+//     K = 16 sources, N = 32: E_hi*[q_hi | q_lo], then N = 16: E_lo*q_hi), and
+//   * the MN-major A operand of the transposed product with M = 128 rows =
+//     [E_hi of the 64 sources ; E_lo of the 64 sources], K = 16 targets,
+//     N = 32 ([q_hi | q_lo] of T): one MMA per K step.
+// The tensor core rounds its FP32 accumulator toward zero at every MMA, so
+// the large hi*hi terms get their own columns with one update per K step.
+//
+// Accumulation.  The forward sums of T stay in the CTA: TMEM accumulators per
+// (upper entry, 128-target tile), folded into Kahan-compensated running sums
+// in shared memory and written once.  The transposed sums of S (64 sources x
+// 16 right-hand sides per chunk) are combined from the hi and lo rows and
+// added to a 64-bit fixed-point accumulator per site with
+// red.global.add.u64: integer addition is associative, so the result does
+// not depend on the order in which CTAs finish (repeated matvecs are bit
+// identical).  The fixed-point step 2^-sb is chosen from a bound on every
+// partial sum (N sites times the largest E'), far below the FP32 rounding.
+// A finishing kernel adds both parts and applies the point factors.
+//
+// Roles: 16 compute warps, one warp whose lane 0 issues the MMAs, one whose
+// lane 0 issues the TMA bulk copies; hand-over through mbarriers only; every
+// wait is bounded and raises the plan's error flag instead of hanging.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdint>
+#include <vector>
+
+#include <cuda_fp16.h>
+
+#include "dwfmm_internal.cuh"
+#include "tcgen05_util.cuh"
+
+namespace dw {
+
+namespace {
+
+using namespace tc;
+
+constexpr int kSymCompWarps = 16;
+constexpr int kSymThreads = (kSymCompWarps + 2) * 32;
+constexpr int kChunk = 64;          // sources per chunk
+constexpr int kStages = 3;          // TMA stages (coordinates + FP16 charges of one chunk)
+constexpr int kTmemCols = 256;      // forward 2 entries x 2 tiles x 32, transposed 2 x 32
+constexpr int kQChunkBytes = kChunk * 16 * 2 * 2;   // [s/8][4 cores][128 B]: 4 KB
+
+// Instruction descriptor, kind::f16: D F32, A and B F16; a_mn = 1 reads A
+// MN-major.
+__host__ __device__ constexpr uint32_t idesc_f16(uint32_t m, uint32_t n, uint32_t a_mn) {
+  return (1u << 4) | (a_mn << 15) | ((n >> 3) << 17) | ((m >> 4) << 24);
+}
+constexpr uint32_t kIdFwd32 = idesc_f16(128, 32, 0);
+constexpr uint32_t kIdFwd16 = idesc_f16(128, 16, 0);
+constexpr uint32_t kIdTrn32 = idesc_f16(128, 32, 1);
+
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, u64 adesc, u64 bdesc, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
+          d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
+}
+
+// E tile of one chunk: core (t/8, hl, s/8) at (t/8)*2048 + hl*1024 + (s/8)*128,
+// row t%8 at 16 bytes, 8 FP16 sources per row.
+constexpr int kTS = 2048, kHL = 1024;
+// Descriptor of the transposed (MN-major) A operand: for this layout the
+// leading byte offset is the stride between core matrices along K (targets,
+// kTS) and the stride byte offset the one along M (sources, 128 bytes).
+constexpr uint32_t kSymTrnLbo = kTS, kSymTrnSbo = 128;
+
+template <int KER>
+__device__ __forceinline__ float phi_sym(float a) {
+  if (KER == DWFMM_K_GAUSS) return ex2f(a);
+  const float r = sqrtf_a(a);
+  if (KER == DWFMM_K_EXP) return ex2f(-r);
+  const float e = ex2f(-1.4426950408889634f * r);
+  return fmaf(r, e, e);
+}
+
+// E' for two targets (A, B) and sources j..j+7 of the stage (row stride 64
+// floats); results as FP16 hi / lo rows (4 words each).
+template <int D, int KER>
+__device__ __forceinline__ void eval8x2(const float* sc, int j, const u64* xa, const u64* xb, uint32_t* ha,
+                                        uint32_t* la, uint32_t* hb, uint32_t* lb) {
+  u64 pa[4], pb[4];
+  if (KER == DWFMM_K_GAUSS) {
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const ulonglong2 v0 = *reinterpret_cast<const ulonglong2*>(sc + k * kChunk + j);
+      const ulonglong2 v1 = *reinterpret_cast<const ulonglong2*>(sc + k * kChunk + j + 4);
+      if (k == 0) {
+        pa[0] = mul2(xa[0], v0.x); pa[1] = mul2(xa[0], v0.y); pa[2] = mul2(xa[0], v1.x); pa[3] = mul2(xa[0], v1.y);
+        pb[0] = mul2(xb[0], v0.x); pb[1] = mul2(xb[0], v0.y); pb[2] = mul2(xb[0], v1.x); pb[3] = mul2(xb[0], v1.y);
+      } else {
+        pa[0] = fma2(xa[k], v0.x, pa[0]); pa[1] = fma2(xa[k], v0.y, pa[1]);
+        pa[2] = fma2(xa[k], v1.x, pa[2]); pa[3] = fma2(xa[k], v1.y, pa[3]);
+        pb[0] = fma2(xb[k], v0.x, pb[0]); pb[1] = fma2(xb[k], v0.y, pb[1]);
+        pb[2] = fma2(xb[k], v1.x, pb[2]); pb[3] = fma2(xb[k], v1.y, pb[3]);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) pa[u] = pb[u] = 0ull;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const ulonglong2 v0 = *reinterpret_cast<const ulonglong2*>(sc + k * kChunk + j);
+      const ulonglong2 v1 = *reinterpret_cast<const ulonglong2*>(sc + k * kChunk + j + 4);
+      u64 df;
+      df = sub2(xa[k], v0.x); pa[0] = fma2(df, df, pa[0]);
+      df = sub2(xa[k], v0.y); pa[1] = fma2(df, df, pa[1]);
+      df = sub2(xa[k], v1.x); pa[2] = fma2(df, df, pa[2]);
+      df = sub2(xa[k], v1.y); pa[3] = fma2(df, df, pa[3]);
+      df = sub2(xb[k], v0.x); pb[0] = fma2(df, df, pb[0]);
+      df = sub2(xb[k], v0.y); pb[1] = fma2(df, df, pb[1]);
+      df = sub2(xb[k], v1.x); pb[2] = fma2(df, df, pb[2]);
+      df = sub2(xb[k], v1.y); pb[3] = fma2(df, df, pb[3]);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    float f0, f1;
+    up(pa[u], f0, f1);
+    {
+      const float e0 = phi_sym<KER>(f0), e1 = phi_sym<KER>(f1);
+      const __half2 h = __floats2half2_rn(e0, e1);
+      const float2 hf = __half22float2(h);
+      float l0, l1;
+      up(sub2(pk(e0, e1), pk(hf.x, hf.y)), l0, l1);
+      const __half2 l = __floats2half2_rn(l0, l1);
+      ha[u] = *reinterpret_cast<const uint32_t*>(&h);
+      la[u] = *reinterpret_cast<const uint32_t*>(&l);
+    }
+    up(pb[u], f0, f1);
+    {
+      const float e0 = phi_sym<KER>(f0), e1 = phi_sym<KER>(f1);
+      const __half2 h = __floats2half2_rn(e0, e1);
+      const float2 hf = __half22float2(h);
+      float l0, l1;
+      up(sub2(pk(e0, e1), pk(hf.x, hf.y)), l0, l1);
+      const __half2 l = __floats2half2_rn(l0, l1);
+      hb[u] = *reinterpret_cast<const uint32_t*>(&h);
+      lb[u] = *reinterpret_cast<const uint32_t*>(&l);
+    }
+  }
+}
+
+__device__ __forceinline__ void sts128(uint32_t addr, const uint32_t* v) {
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3])
+               : "memory");
+}
+
+__device__ __forceinline__ void red_add_u64(unsigned long long* p, long long v) {
+  asm volatile("red.global.add.u64 [%0], %1;" ::"l"(p), "l"(static_cast<unsigned long long>(v)) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld4x2(uint32_t ta, uint32_t tb, uint32_t* r, uint32_t* q) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(ta));
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(q[0]), "=r"(q[1]), "=r"(q[2]), "=r"(q[3])
+               : "r"(tb));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+struct SymArgs {
+  const float* pts;          // scaled blocks [L][D+1][ld] (coordinates, row D = |x'|^2)
+  int64_t gstride;           // (D+1) * ld
+  const uint16_t* bq;        // FP16 charge blocks [L][ld/8][4][64] (hi r0-7, hi r8-15, lo r0-7, lo r8-15)
+  const int32_t* uprow;      // [L+1] upper entries of each target leaf
+  const int32_t* ups;        // [nup] source leaf of each upper entry (ascending, the first is T itself)
+  const int32_t* order;      // [L] target leaves, longest upper row first
+  float* fwd;                // [L][16][ld] forward sums (normalised units)
+  unsigned long long* acc;   // [L][16][ld] fixed-point transposed sums
+  float acc_scale;           // 2^sb
+  int ld;                    // 128 or 256
+  int* err;
+};
+
+template <int D, int KER>
+__global__ void __launch_bounds__(kSymThreads, 1) k_near_sym_tc(SymArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bars[32];
+  __shared__ uint32_t tmem_slot;
+  uint64_t* full = bars;            // [3] TMA landed
+  uint64_t* sfree = bars + 3;       // [3] stage consumed (16 warps + MMA commit)
+  uint64_t* efull = bars + 6;       // [2] E tile written (16 warps)
+  uint64_t* efree = bars + 8;       // [2] E tile read by the MMAs (commit)
+  uint64_t* tfull = bars + 10;      // [2] transposed accumulator complete (commit)
+  uint64_t* tempty = bars + 12;     // [2] transposed accumulator drained (16 warps)
+  uint64_t* cready = bars + 14;     // [2] lo rows combined into shared memory (8 warps)
+  uint64_t* ffull = bars + 16;      // [2] forward accumulators of an entry complete (commit)
+  uint64_t* fempty = bars + 18;     // [2] forward accumulators folded (16 warps)
+  uint64_t* qfull = bars + 20;      // q_T landed
+  uint64_t* fin = bars + 21;        // every MMA done
+
+  const int ld = a.ld;
+  const int NT = ld / 128;                    // 128-target tiles
+  const int NC = ld / kChunk;                 // chunks per source leaf
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int T = a.order[blockIdx.x];
+  const int e0 = a.uprow[T], ne = a.uprow[T + 1] - e0;
+
+  // shared memory carve-up
+  const uint32_t ebytes = static_cast<uint32_t>(NT * 16 * kTS);        // one E tile
+  const uint32_t coord_bytes = static_cast<uint32_t>(D * kChunk * 4);
+  const uint32_t qoff = (coord_bytes + 1023u) & ~1023u;
+  const uint32_t stage_bytes = qoff + kQChunkBytes;
+  unsigned char* ebuf = smem;                                       // 2 tiles
+  unsigned char* stages = smem + 2 * ebytes;                         // kStages
+  unsigned char* qT = stages + kStages * stage_bytes;               // ld * 64 bytes
+  float* ksum = reinterpret_cast<float*>(qT + ld * 64);              // [NT][16][128] sums, then compensations
+  float* comb = ksum + 2 * NT * 16 * 128;                            // [2][16][64]
+
+  if (t == 0) {
+    for (int i = 0; i < kStages; ++i) {
+      bar_init(&full[i], 1);
+      bar_init(&sfree[i], kSymCompWarps + 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      bar_init(&efull[i], kSymCompWarps);
+      bar_init(&efree[i], 1);
+      bar_init(&tfull[i], 1);
+      bar_init(&tempty[i], kSymCompWarps);
+      bar_init(&cready[i], kSymCompWarps / 2);
+      bar_init(&ffull[i], 1);
+      bar_init(&fempty[i], kSymCompWarps);
+    }
+    bar_init(qfull, 1);
+    bar_init(fin, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tmem_alloc(&tmem_slot, kTmemCols);
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = tmem_slot;
+
+  if (warp == kSymCompWarps + 1) {
+    // ---- TMA producer
+    if (lane == 0) {
+      bool bad = false;
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      bar_expect_tx(qfull, static_cast<uint32_t>(ld * 64));
+      bulk_load(qT, a.bq + static_cast<int64_t>(T) * ld * 32, static_cast<uint32_t>(ld * 64), qfull);
+      int i = 0;
+      for (int e = 0; e < ne && !bad; ++e) {
+        const int S = a.ups[e0 + e];
+        for (int c = 0; c < NC; ++c, ++i) {
+          const int st = i % kStages;
+          if (i >= kStages && !wait_sleep(&sfree[st], static_cast<uint32_t>(((i - kStages) / kStages) & 1))) {
+            bad = true;
+            break;
+          }
+          unsigned char* dst = stages + st * stage_bytes;
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          bar_expect_tx(&full[st], coord_bytes + kQChunkBytes);
+          const float* src = a.pts + static_cast<int64_t>(S) * a.gstride + c * kChunk;
+#pragma unroll 1
+          for (int k = 0; k < D; ++k) bulk_load(dst + k * kChunk * 4, src + static_cast<int64_t>(k) * ld, kChunk * 4,
+                                                &full[st]);
+          bulk_load(dst + qoff, a.bq + (static_cast<int64_t>(S) * ld + c * kChunk) * 32, kQChunkBytes, &full[st]);
+        }
+      }
+      // copies in flight land before the CTA exits
+      (void)wait_sleep(qfull, 0u);
+      for (int j = i > kStages ? i - kStages : 0; j < i; ++j)
+        (void)wait_sleep(&full[j % kStages], static_cast<uint32_t>((j / kStages) & 1));
+      if (bad) atomicExch(a.err, 3);
+    }
+  } else if (warp == kSymCompWarps) {
+    // ---- MMA issuer
+    if (lane == 0) {
+      bool bad = !wait_sleep(qfull, 0u);
+      const uint32_t ebase = sptr(ebuf), sbase = sptr(stages), qtb = sptr(qT);
+      int i = 0, jt = 0;
+      for (int e = 0; e < ne && !bad; ++e) {
+        const int S = a.ups[e0 + e];
+        const bool diag = S == T;
+        const int fb = e & 1;
+        for (int c = 0; c < NC; ++c, ++i) {
+          const int st = i % kStages, eb = i & 1;
+          if (!wait_sleep(&full[st], static_cast<uint32_t>((i / kStages) & 1)) ||
+              !wait_sleep(&efull[eb], static_cast<uint32_t>((i >> 1) & 1)) ||
+              (c == 0 && e >= 2 && !wait_sleep(&fempty[fb], static_cast<uint32_t>(((e - 2) >> 1) & 1)))) {
+            bad = true;
+            break;
+          }
+          fence_after();
+          const uint32_t et = ebase + eb * ebytes;
+          const uint32_t qs = sbase + st * stage_bytes + qoff;
+          // forward: D[t][r] over the chunk's sources, K = 16 per MMA
+          for (int at = 0; at < NT; ++at) {
+            const uint32_t dcol = tmem + static_cast<uint32_t>(fb * 64 + at * 32);
+            for (int kk = 0; kk < kChunk / 16; ++kk) {
+              const uint32_t aoff = et + at * 16 * kTS + kk * 2 * 128;
+              const u64 ahi = smem_desc(aoff, 128, kTS);
+              const u64 alo = smem_desc(aoff + kHL, 128, kTS);
+              const u64 bq = smem_desc(qs + kk * 2 * 512, 512, 128);
+              mma_f16(dcol, ahi, bq, kIdFwd32, (c > 0 || kk > 0) ? 1u : 0u);
+              mma_f16(dcol + 16, alo, bq, kIdFwd16, 1u);
+            }
+          }
+          if (!diag) {
+            const int tb = jt & 1;
+            if (jt >= 2 && !wait_sleep(&tempty[tb], static_cast<uint32_t>(((jt - 2) >> 1) & 1))) {
+              bad = true;
+              break;
+            }
+            fence_after();
+            const uint32_t dcol = tmem + static_cast<uint32_t>(128 + tb * 32);
+            for (int j = 0; j < NT * 8; ++j) {
+              // A: rows [E_hi of 64 sources ; E_lo of 64 sources], MN-major
+              const u64 at = smem_desc(et + j * 2 * kTS, kSymTrnLbo, kSymTrnSbo);
+              const u64 bq = smem_desc(qtb + j * 2 * 512, 512, 128);
+              mma_f16(dcol, at, bq, kIdTrn32, j > 0 ? 1u : 0u);
+            }
+            mma_commit(&tfull[tb]);
+            ++jt;
+          }
+          mma_commit(&efree[eb]);
+          mma_commit(&sfree[st]);
+          if (c == NC - 1) mma_commit(&ffull[fb]);
+        }
+      }
+      mma_commit(fin);
+      (void)wait_sleep(fin, 0u);
+      if (bad) atomicExch(a.err, 3);
+    }
+  } else {
+    // ---- compute warps
+    const int qd = warp & 3, part = warp >> 2;   // TMEM lane quadrant, source quarter of a chunk
+    const int ta = qd * 32 + lane;               // targets ta and ta + 128 (tile 1, if NT == 2)
+    const float* tp = a.pts + static_cast<int64_t>(T) * a.gstride;
+    u64 xa[D], xb[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      float va = tp[k * ld + ta];
+      float vb = NT == 2 ? tp[k * ld + ta + 128] : va;
+      if (KER == DWFMM_K_GAUSS) {
+        va *= 2.0f;
+        vb *= 2.0f;
+      }
+      xa[k] = pk(va, va);
+      xb[k] = pk(vb, vb);
+    }
+    // Kahan sums: warp (qd, part) owns tile part / 2, right-hand sides 8 (part % 2) .. + 7
+    const int ftile = part >> 1, fr0 = 8 * (part & 1);
+    const bool fown = ftile < NT;
+    if (fown) {
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        ksum[(ftile * 16 + fr0 + r) * 128 + ta] = 0.0f;
+        ksum[NT * 16 * 128 + (ftile * 16 + fr0 + r) * 128 + ta] = 0.0f;
+      }
+    }
+    const uint32_t lane_base = tmem + (static_cast<uint32_t>(qd * 32) << 16);
+    bool bad = false;
+
+    // fold the forward accumulators of entry e into the sums
+    auto fold = [&](int e) {
+      const int fb = e & 1;
+      const bool ok = wait_sleep(&ffull[fb], static_cast<uint32_t>((e >> 1) & 1));
+      if (__any_sync(0xffffffffu, !ok)) {
+        bad = true;
+        return;
+      }
+      fence_after();
+      if (fown) {
+        uint32_t dv[8], dl[8];
+        const uint32_t col = lane_base + static_cast<uint32_t>(fb * 64 + ftile * 32 + fr0);
+        tmem_ld8x2(col, col + 16, dv, dl);
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+          float* pa = ksum + (ftile * 16 + fr0 + r) * 128 + ta;
+          const float acc = pa[0], comp = pa[NT * 16 * 128];
+          const float y = (__uint_as_float(dv[r]) + __uint_as_float(dl[r])) - comp;
+          const float s = acc + y;
+          pa[NT * 16 * 128] = (s - acc) - y;
+          pa[0] = s;
+        }
+      }
+      fence_before();
+      __syncwarp();
+      if (lane == 0) bar_arrive(&fempty[fb]);
+    };
+    // drain transposed accumulator jt (chunk c of source leaf S) into the
+    // fixed-point sums of S
+    auto flush = [&](int jt, int S, int c) {
+      const int tb = jt & 1;
+      const bool ok = wait_sleep(&tfull[tb], static_cast<uint32_t>((jt >> 1) & 1));
+      if (__any_sync(0xffffffffu, !ok)) {
+        bad = true;
+        return;
+      }
+      fence_after();
+      const int r0 = 4 * part;
+      const uint32_t col = lane_base + static_cast<uint32_t>(128 + tb * 32 + r0);
+      uint32_t x[4], y[4];
+      tmem_ld4x2(col, col + 16, x, y);
+      float* cb = comb + tb * (64 * 16);
+      if (qd >= 2) {
+        // rows 64..127: E_lo of source 32 (qd - 2) + lane
+        const int s = (qd - 2) * 32 + lane;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) cb[(r0 + j) * 64 + s] = __uint_as_float(x[j]) + __uint_as_float(y[j]);
+        fence_before();
+        __syncwarp();
+        if (lane == 0) {
+          bar_arrive(&cready[tb]);
+          bar_arrive(&tempty[tb]);
+        }
+      } else {
+        const int s = qd * 32 + lane;
+        const bool okc = wait_sleep(&cready[tb], static_cast<uint32_t>((jt >> 1) & 1));
+        if (__any_sync(0xffffffffu, !okc)) {
+          bad = true;
+          fence_before();
+          if (lane == 0) bar_arrive(&tempty[tb]);
+          return;
+        }
+        unsigned long long* dst = a.acc + (static_cast<int64_t>(S) * 16 + r0) * ld + c * kChunk + s;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float v = (__uint_as_float(x[j]) + __uint_as_float(y[j])) + cb[(r0 + j) * 64 + s];
+          red_add_u64(dst + static_cast<int64_t>(j) * ld, __float2ll_rn(v * a.acc_scale));
+        }
+        fence_before();
+        __syncwarp();
+        if (lane == 0) bar_arrive(&tempty[tb]);
+      }
+    };
+
+    int i = 0, jt = 0;
+    int pend_jt = -1, pend_S = 0, pend_c = 0;
+    for (int e = 0; e < ne && !bad; ++e) {
+      const int S = a.ups[e0 + e];
+      const bool diag = S == T;
+      for (int c = 0; c < NC; ++c, ++i) {
+        const int st = i % kStages, eb = i & 1;
+        const bool ok = wait_sleep(&full[st], static_cast<uint32_t>((i / kStages) & 1)) &&
+                        (i < 2 || wait_sleep(&efree[eb], static_cast<uint32_t>(((i - 2) >> 1) & 1)));
+        if (__any_sync(0xffffffffu, !ok)) {
+          bad = true;
+          break;
+        }
+        const float* sc = reinterpret_cast<const float*>(stages + st * stage_bytes);
+        const uint32_t et = sptr(ebuf + eb * ebytes);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int j = part * 16 + h * 8;   // source within the chunk
+          uint32_t ha[4], la[4], hb[4], lb[4];
+          eval8x2<D, KER>(sc, j, xa, xb, ha, la, hb, lb);
+          const uint32_t off = static_cast<uint32_t>((ta >> 3) * kTS + (j >> 3) * 128 + (ta & 7) * 16);
+          sts128(et + off, ha);
+          sts128(et + off + kHL, la);
+          if (NT == 2) {
+            sts128(et + off + 16 * kTS, hb);
+            sts128(et + off + 16 * kTS + kHL, lb);
+          }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) {
+          bar_arrive(&efull[eb]);
+          bar_arrive(&sfree[st]);
+        }
+        // service: the previous chunk's transposed sums, the previous entry's forward sums
+        if (pend_jt >= 0) {
+          flush(pend_jt, pend_S, pend_c);
+          pend_jt = -1;
+          if (bad) break;
+        }
+        if (c == 0 && e >= 1) {
+          fold(e - 1);
+          if (bad) break;
+        }
+        if (!diag) {
+          pend_jt = jt;
+          pend_S = S;
+          pend_c = c;
+          ++jt;
+        }
+      }
+    }
+    if (!bad && pend_jt >= 0) flush(pend_jt, pend_S, pend_c);
+    if (!bad && ne >= 1) fold(ne - 1);
+    if (bad && lane == 0) atomicExch(a.err, 3);
+    if (fown) {
+      float* op = a.fwd + static_cast<int64_t>(T) * 16 * ld + ftile * 128 + ta;
+#pragma unroll
+      for (int r = 0; r < 8; ++r) op[(fr0 + r) * ld] = ksum[(ftile * 16 + fr0 + r) * 128 + ta];
+    }
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 0) tmem_dealloc(tmem, kTmemCols);
+}
+
+// Per right-hand side: the largest |q * factor| (float bits, atomicMax).
+__global__ void k_sym_colmax(const float* xb, const float* pts, int64_t gstride, int L, int ld, int D, int gauss,
+                             int Rc, unsigned* colmax) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t n = static_cast<int64_t>(L) * ld;
+  float m[16];
+#pragma unroll
+  for (int r = 0; r < 16; ++r) m[r] = 0.0f;
+  for (int64_t p = i; p < n; p += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t g = p / ld;
+    const int s = static_cast<int>(p % ld);
+    const float f = gauss ? exp2f(-pts[g * gstride + static_cast<int64_t>(D) * ld + s]) : 1.0f;
+    for (int r = 0; r < Rc; ++r) m[r] = fmaxf(m[r], fabsf(xb[(g * 16 + r) * ld + s] * f));
+  }
+  for (int r = 0; r < Rc; ++r) {
+    float v = m[r];
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0 && v > 0.0f) atomicMax(&colmax[r], __float_as_uint(v));
+  }
+}
+
+// Power of two that brings the column's largest |q'| into [0.5, 1).
+__device__ __forceinline__ float col_scale_exp(unsigned bits, int* e) {
+  const float m = __uint_as_float(bits);
+  int ex = 0;
+  if (m > 0.0f) (void)frexpf(m, &ex);
+  *e = ex;
+  return ldexpf(1.0f, -ex);
+}
+
+// FP16 hi / lo charge blocks: q' = q * factor * 2^-e_r, core (s/8, n/8) at
+// (s/8)*512 + (n/8)*128, row n%8 at 16 bytes, source s%8 at 2 bytes; n < 16
+// hi, n >= 16 lo.
+__global__ void k_sym_make_bq(const float* xb, const float* pts, int64_t gstride, int L, int ld, int D, int gauss,
+                              int Rc, const unsigned* colmax, uint16_t* bq) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= static_cast<int64_t>(L) * ld * 16) return;
+  const int r = static_cast<int>(i % 16);
+  const int64_t gs = i / 16;
+  const int s = static_cast<int>(gs % ld);
+  const int64_t g = gs / ld;
+  float v = 0.0f;
+  if (r < Rc) {
+    int ex;
+    const float sc = col_scale_exp(colmax[r], &ex);
+    const float f = gauss ? exp2f(-pts[g * gstride + static_cast<int64_t>(D) * ld + s]) : 1.0f;
+    v = xb[(g * 16 + r) * ld + s] * f * sc;
+  }
+  const __half h = __float2half_rn(v);
+  const __half l = __float2half_rn(v - __half2float(h));
+  uint16_t* blk = bq + g * static_cast<int64_t>(ld) * 32;
+  const int64_t base = (s / 8) * 256 + (s % 8);               // in 2-byte units
+  blk[base + (r / 8) * 64 + (r % 8) * 8] = __half_as_ushort(h);
+  blk[base + (2 + r / 8) * 64 + (r % 8) * 8] = __half_as_ushort(l);
+}
+
+// y_near = (forward + fixed-point transposed) * 2^e_r * factor(t).
+__global__ void k_sym_finish(const float* fwd, const unsigned long long* acc, double inv_scale, const float* pts,
+                             int64_t gstride, int L, int ld, int D, int gauss, int Rc, const unsigned* colmax,
+                             float* ynear, int64_t ystride) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= static_cast<int64_t>(L) * 16 * ld) return;
+  const int s = static_cast<int>(i % ld);
+  const int r = static_cast<int>((i / ld) % 16);
+  const int64_t g = i / (16 * static_cast<int64_t>(ld));
+  if (r >= Rc) return;
+  int ex;
+  (void)col_scale_exp(colmax[r], &ex);
+  const double tr = static_cast<double>(static_cast<long long>(acc[i])) * inv_scale;
+  double v = (static_cast<double>(fwd[i]) + tr) * ldexp(1.0, ex);
+  if (gauss) v *= static_cast<double>(exp2f(-pts[g * gstride + static_cast<int64_t>(D) * ld + s]));
+  ynear[g * ystride + static_cast<int64_t>(r) * ld + s] = static_cast<float>(v);
+}
+
+size_t sym_smem(int D, int ld) {
+  const int NT = ld / 128;
+  const size_t ebytes = static_cast<size_t>(NT) * 16 * kTS;
+  const size_t coord = static_cast<size_t>(D) * kChunk * 4;
+  const size_t stage = ((coord + 1023) & ~size_t(1023)) + kQChunkBytes;
+  return 2 * ebytes + kStages * stage + static_cast<size_t>(ld) * 64 + 2 * NT * 16 * 128 * 4 + 2 * 64 * 16 * 4;
+}
+
+template <int D>
+void sym_launch_d(int kernel, const SymArgs& a, int grid, size_t smem, cudaStream_t s) {
+  switch (kernel) {
+    case DWFMM_K_EXP: k_near_sym_tc<D, DWFMM_K_EXP><<<grid, kSymThreads, smem, s>>>(a); break;
+    case DWFMM_K_MATERN32: k_near_sym_tc<D, DWFMM_K_MATERN32><<<grid, kSymThreads, smem, s>>>(a); break;
+    default: k_near_sym_tc<D, DWFMM_K_GAUSS><<<grid, kSymThreads, smem, s>>>(a);
+  }
+}
+
+template <int D>
+void sym_attrs_d(int bytes) {
+  cudaFuncSetAttribute(k_near_sym_tc<D, DWFMM_K_EXP>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute(k_near_sym_tc<D, DWFMM_K_MATERN32>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute(k_near_sym_tc<D, DWFMM_K_GAUSS>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+std::atomic<uint64_t> g_sym_attrs_dev{0};
+constexpr int kSymSmemMax = 220 * 1024;
+
+}  // namespace
+
+// Rows of the symmetric tensor-core near field: target leaves in order of
+// decreasing upper-list length (longest first, so the short rows fill the
+// tail of the launch).  Host counts of the upper rows come from the tree
+// build.
+void sym_tc_order(Plan& P, const std::vector<int>& upper_counts) {
+  std::vector<int32_t> ord(P.L);
+  for (int i = 0; i < P.L; ++i) ord[i] = i;
+  std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return upper_counts[x] > upper_counts[y]; });
+  P.sym_order.alloc(P.L);
+  DW_CUDA(cudaMemcpyAsync(P.sym_order.p, ord.data(), sizeof(int32_t) * P.L, cudaMemcpyHostToDevice, P.stream));
+  DW_CUDA(cudaStreamSynchronize(P.stream));
+}
+
+// Whether the symmetric tensor-core near field applies: MIXED with 9..16
+// right-hand sides, a symmetric near list, leaves of 128 or 256 slots, a
+// padded dimension the kernel is built for, and E' inside the FP16 range.
+bool sym_tc_eligible(const Plan& P, int D, int RC) {
+  if (P.prec != DWFMM_P_MIXED || RC != 16 || !P.sym_ok || P.sym_nup <= 0 || !P.sym_order.p) return false;
+  if (P.m_pad != 128 && P.m_pad != 256) return false;
+  if (D != 4 && D != 8 && D != 10 && D != 12 && D != 16 && D != 20) return false;
+  if (P.kernel == DWFMM_K_GAUSS && !(P.gauss_fact && 2.0 * P.gauss_bound <= 15.0)) return false;
+  return sym_smem(D, P.m_pad) <= static_cast<size_t>(kSymSmemMax);
+}
+
+// Fixed-point bits of the transposed sums: every partial sum is at most N
+// sites times the largest E' times max |q'| <= 1.
+int sym_tc_bits(const Plan& P) {
+  const double emax = P.kernel == DWFMM_K_GAUSS ? std::exp2(2.0 * P.gauss_bound) : 1.0;
+  const double bound = static_cast<double>(std::max<int64_t>(P.N, 1)) * emax * 2.0;
+  return 62 - static_cast<int>(std::ceil(std::log2(bound)));
+}
+
+bool near_sym_tc(Plan& P, int D, int Rc, cudaStream_t s) {
+  const int RC = 16;
+  if (!sym_tc_eligible(P, D, RC)) return false;
+  const uint64_t dbit = device_bit();
+  if (!(g_sym_attrs_dev.load() & dbit)) {
+    sym_attrs_d<4>(kSymSmemMax);
+    sym_attrs_d<8>(kSymSmemMax);
+    sym_attrs_d<10>(kSymSmemMax);
+    sym_attrs_d<12>(kSymSmemMax);
+    sym_attrs_d<16>(kSymSmemMax);
+    sym_attrs_d<20>(kSymSmemMax);
+    DW_CUDA(cudaGetLastError());
+    g_sym_attrs_dev.fetch_or(dbit);
+  }
+  const int ld = P.m_pad;
+  const int64_t nsite = static_cast<int64_t>(P.L) * 16 * ld;
+  const int64_t gstride = static_cast<int64_t>(D + 1) * ld;
+  const int gauss = P.kernel == DWFMM_K_GAUSS ? 1 : 0;
+  P.sym_bq16.alloc(static_cast<size_t>(P.L) * ld * 32);
+  P.sym_acc.alloc(static_cast<size_t>(nsite));
+  P.sym_fwd.alloc(static_cast<size_t>(nsite));
+  P.sym_colmax.alloc(16);
+  DW_CUDA(cudaMemsetAsync(P.sym_colmax.p, 0, 16 * sizeof(unsigned), s));
+  DW_CUDA(cudaMemsetAsync(P.sym_acc.p, 0, static_cast<size_t>(nsite) * sizeof(unsigned long long), s));
+  k_sym_colmax<<<2 * sm_count(), 256, 0, s>>>(P.xb32.p, P.d_ptsk.p, gstride, P.L, ld, D, gauss, Rc,
+                                               P.sym_colmax.p);
+  k_sym_make_bq<<<ceil_div(static_cast<int64_t>(P.L) * ld * 16, 256), 256, 0, s>>>(
+      P.xb32.p, P.d_ptsk.p, gstride, P.L, ld, D, gauss, Rc, P.sym_colmax.p, P.sym_bq16.p);
+  const int sb = sym_tc_bits(P);
+  SymArgs a{};
+  a.pts = P.d_ptsk.p;
+  a.gstride = gstride;
+  a.bq = P.sym_bq16.p;
+  a.uprow = P.sym_uprow.p;
+  a.ups = P.sym_s.p;
+  a.order = P.sym_order.p;
+  a.fwd = P.sym_fwd.p;
+  a.acc = P.sym_acc.p;
+  a.acc_scale = std::ldexp(1.0f, sb);
+  a.ld = ld;
+  a.err = P.d_err.p;
+  const size_t smem = sym_smem(D, ld);
+  switch (D) {
+    case 4: sym_launch_d<4>(P.kernel, a, P.L, smem, s); break;
+    case 8: sym_launch_d<8>(P.kernel, a, P.L, smem, s); break;
+    case 10: sym_launch_d<10>(P.kernel, a, P.L, smem, s); break;
+    case 12: sym_launch_d<12>(P.kernel, a, P.L, smem, s); break;
+    case 16: sym_launch_d<16>(P.kernel, a, P.L, smem, s); break;
+    default: sym_launch_d<20>(P.kernel, a, P.L, smem, s); break;
+  }
+  DW_CUDA(cudaGetLastError());
+  k_sym_finish<<<ceil_div(nsite, 256), 256, 0, s>>>(P.sym_fwd.p, P.sym_acc.p, std::ldexp(1.0, -sb), P.d_ptsk.p,
+                                                     gstride, P.L, ld, D, gauss, Rc, P.sym_colmax.p, P.ynear32.p,
+                                                     static_cast<int64_t>(kRC) * ld);
+  DW_CUDA(cudaGetLastError());
+  return true;
+}
+
+}  // namespace dw

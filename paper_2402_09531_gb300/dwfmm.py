@@ -32,7 +32,7 @@ PHASES = ("gather", "p2m_m2m", "m2l", "l2l_l2p", "p2p", "scatter", "matvec")
 # Every entry point declared in include/dwfmm.h.
 EXPORTS = ("dwfmm_plan_create", "dwfmm_plan_set_nodes", "dwfmm_tree_build", "dwfmm_matvec",
            "dwfmm_solve", "dwfmm_plan_destroy", "dwfmm_status_string", "dwfmm_last_error",
-           "dwfmm_plan_info", "dwfmm_plan_export", "dwfmm_tree_export", "dwfmm_lists_export",
+           "dwfmm_plan_info", "dwfmm_near_engine", "dwfmm_plan_export", "dwfmm_tree_export", "dwfmm_lists_export",
            "dwfmm_set_profiling", "dwfmm_phase_times", "dwfmm_direct_sum_noalloc",
            "dwfmm_cg_begin", "dwfmm_cg_step", "dwfmm_cg_poll", "dwfmm_cg_result", "dwfmm_residual",
            "dwfmm_refine",
@@ -71,6 +71,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "dwfmm_status_string": (C.c_char_p, [i32]),
         "dwfmm_last_error": (C.c_char_p, [P]),
         "dwfmm_plan_info": (i32, [P, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), C.POINTER(i32)]),
+        "dwfmm_near_engine": (i32, [P, C.POINTER(i32)]),
         "dwfmm_plan_export": (i32, [P, P, P, P, P, P]),
         "dwfmm_tree_export": (i32, [P, P, P, P, P, P]),
         "dwfmm_lists_export": (i32, [P, P, P]),
@@ -329,6 +330,15 @@ class Plan:
         nx, nf, nn, dep = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int32()
         self.check(self._l.dwfmm_plan_info(self.h, C.byref(nx), C.byref(nf), C.byref(nn), C.byref(dep)))
         return int(nx.value), int(nf.value), int(nn.value), int(dep.value)
+
+    NEAR_ENGINES = {-1: "none", 0: "fp64_list", 1: "fp64_symmetric", 2: "fp32_cuda_cores",
+                    3: "mixed_tf32_tensor", 4: "mixed_symmetric_fp16_tensor"}
+
+    def near_engine(self) -> str:
+        """Engine that evaluated the near field in the last matvec."""
+        e = C.c_int32(-1)
+        self.check(self._l.dwfmm_near_engine(self.h, C.byref(e)))
+        return self.NEAR_ENGINES.get(int(e.value), str(e.value))
 
     def export_expansion(self):
         n, d = self.n_x, self.d

@@ -395,6 +395,41 @@ def test_mixed_tensor_core_d10_workload_shape():
     assert o.rel_err(y, o.fmm_matvec(pb, f)) <= FP32_TOL
 
 
+@pytest.mark.parametrize("kernel,n,leaf,nrhs,q", [("gauss", 8000, 256, 16, 4.0), ("exp", 4096, 128, 16, 4.0),
+                                                    ("matern32", 8192, 256, 9, 4.0), ("gauss", 4000, 128, 12, 5.0)])
+def test_mixed_symmetric_near_field_matches_oracle(kernel, n, leaf, nrhs, q):
+    """Leaves of 128 or 256 slots (full or ragged: 8000 sites give 250 per
+    leaf, 4000 give 125): each unordered near pair of leaves is evaluated once
+    on the tensor cores (FP16 hi/lo), the transposed sums go through 64-bit
+    fixed-point reductions.  Matches the oracle within the float32 tolerance,
+    and repeated matvecs are bit-identical."""
+    torch = _torch()
+    w, X, f, pb = _case("mixed", n, seed=37, kernel=kernel, q=q, leaf=leaf, nrhs=nrhs)
+    plan, y = _gpu_matvec(w, X, f, pb, "mixed")
+    assert plan.near_engine() == "mixed_symmetric_fp16_tensor"
+    assert np.all(np.isfinite(y))
+    assert o.rel_err(y, o.fmm_matvec(pb, f)) <= FP32_TOL
+    xd = torch.from_numpy(f).cuda()
+    y2 = torch.full_like(xd, float("nan"))
+    plan.matvec(xd, y2)
+    torch.cuda.synchronize()
+    assert np.array_equal(y2.cpu().numpy(), y)
+    plan.close()
+
+
+def test_mixed_symmetric_near_field_dense_against_brute_force():
+    """eta large: no admissible pair, every leaf pair is near, and the matvec
+    is the exact dense product (the fp16 hi/lo split and the fixed-point
+    transposed sums against the oracle's brute force)."""
+    w, X, f, pb = _case("mixed", 4096, seed=38, kernel="gauss", q=2.0, leaf=256, nrhs=16, eta=1e9)
+    plan, y = _gpu_matvec(w, X, f, pb, "mixed")
+    assert plan.near_engine() == "mixed_symmetric_fp16_tensor"
+    assert plan.info()[1] == 0
+    ref = o.dense_matvec(w.kernel, X, f, w.sigma)
+    assert o.rel_err(y, ref) <= FP32_TOL
+    plan.close()
+
+
 @pytest.mark.parametrize("sigma", [0.1, 0.35])
 def test_mixed_gauss_factored_range(sigma):
     """The tensor-core near field evaluates the Gaussian as 2^(2 x'.s') with

@@ -62,3 +62,22 @@ def test_reference_arm_runs_on_rank_zero_only():
                         "--warmup", "0"], env=env, capture_output=True, text=True, timeout=120)
     assert p.returncode == 0, p.stderr[-2000:]
     assert p.stdout.strip() == ""
+
+
+def test_oracle_baseline_uses_one_leaf_per_core():
+    """The CPU baseline runs one target leaf per worker, all stepping
+    together, and reports the cores it used."""
+    sys.path.insert(0, ROOT)
+    import bench
+    res = bench.oracle_sample("small", steps=1, warmup=0, workers=2)
+    assert res["cores"] == 2 and res["leaves"] == 2
+    assert res["rows"] == 2 * 64 and res["units_per_step"] == 2 * 64
+    assert res["s_per_step"] > 0 and res["nproc"] >= 1 and res["cpu_model"]
+
+
+def test_traffic_is_reported_only_for_the_captured_kernel_source():
+    sys.path.insert(0, ROOT)
+    import bench
+    for b, src, sha, wl, fn in bench._traffic_records():
+        assert b > 0 and src.endswith(".cu") and len(sha) == 16
+    assert bench.recorded_traffic("p2p_tc.cu", "no-such-workload") is None
