@@ -244,12 +244,36 @@ def job_throughput(world: int, n: int, nrhs: int, seconds_per_step: float) -> fl
     return world * n * nrhs / seconds_per_step
 
 
-def near_pairs(plan) -> int:
+def near_pairs(plan):
+    """(ordered near pairs of sites, sum over leaves of |leaf|^2): the pairs of
+    every near block (T, S) of Eq. (5.1), and the pairs of its diagonal
+    blocks (T, T)."""
     import numpy as np
     t = plan.export_tree()
     _, near = plan.export_lists()
     size = (t["end"] - t["begin"]).astype(np.int64)
-    return int(np.sum(size[near[:, 0]] * size[near[:, 1]]))
+    diag = near[near[:, 0] == near[:, 1], 0]
+    return int(np.sum(size[near[:, 0]] * size[near[:, 1]])), int(np.sum(size[diag] ** 2))
+
+
+def p2p_accounting(engine: str, pairs: int, diag: int, d: int, R: int):
+    """Algorithmic work of one near-field launch per engine: kernel
+    evaluations (each 3d + 4 FP32 flops: d differences or products, d
+    multiply-adds, ~4 for phi) and where the 2R flops per ordered pair of the
+    contraction run.  The symmetric engine evaluates each unordered pair of
+    sites once: (pairs + diag) / 2 evaluations."""
+    if engine == "mixed_symmetric_fp16_tensor":
+        return {"evals": (pairs + diag) // 2, "flops_per_eval": 3 * d + 4, "tensor": True,
+                "source": "p2p_sym.cu",
+                "kernel": ("p2p (near field): k_near_sym_tc, each unordered near pair of sites evaluated once on "
+                           "the FP32 pipe; both contractions (forward and transposed) on tcgen05 FP16 hi/lo, "
+                           "counted separately below")}
+    if engine == "mixed_tf32_tensor":
+        return {"evals": pairs, "flops_per_eval": 3 * d + 4, "tensor": True, "source": "p2p_tc.cu",
+                "kernel": ("p2p (near field): k_sum_tc, every ordered pair evaluated on the FP32 pipe, "
+                           "contraction on tcgen05 TF32 hi/lo (counted separately below)")}
+    return {"evals": pairs, "flops_per_eval": 3 * d + 4 + 2 * R, "tensor": False, "source": "p2p_f32.cu",
+            "kernel": "p2p (near field): k_sum_f32, evaluation and contraction on the FP32 pipe"}
 
 
 def kernel_source_sha(src: str) -> str:
@@ -362,7 +386,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         tree_ms.append((time.perf_counter() - t0) * 1e3)
     n_x, n_far, n_near, depth = plan.info()
-    pairs = near_pairs(plan)
+    pairs, diag_pairs = near_pairs(plan)
 
     xd = torch.from_numpy(f).to(dev)
     yd = torch.empty_like(xd)
@@ -415,21 +439,19 @@ def run_ours(args):
             e2e_s.append(time.perf_counter() - t0)
     e2e_t = max_over_ranks(dist, dev, statistics.mean(e2e_s))
 
-    # roofline of the dominant kernel (P2P): algorithmic FP32 flops per launch.
-    # MIXED plans with 9..16 RHS contract on the tensor cores (k_sum_tc): the
-    # CUDA cores then carry the kernel evaluation (3d + 4 flops per pair) and
-    # the 2R flops of the contraction run on the tensor pipe.
+    # roofline of the dominant kernel (P2P): algorithmic FP32 flops per launch
+    # (see p2p_accounting); the tensor-pipe flops of the contraction beside it
     p2p_ms, p2p_launches = phases["p2p"]
     p2p_avg_ms = p2p_ms / max(1, p2p_launches)
-    tensor_contraction = args.precision == "mixed" and 8 < R <= 16
-    flops_pair = 3 * d + 4 + (0 if tensor_contraction else 2 * R)
-    achieved = pairs * flops_pair / (p2p_avg_ms / 1e3) / 1e12
+    engine = plan.near_engine()
+    acct = p2p_accounting(engine, pairs, diag_pairs, d, R)
+    achieved = acct["evals"] * acct["flops_per_eval"] / (p2p_avg_ms / 1e3) / 1e12
     peaks = measured_peaks()
     clock_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     peak = sms * FP32_LANES * 2 * clock_mhz * 1e6 / 1e12
     launches = sum(v[1] for k, v in phases.items() if k != "matvec")
-    ksrc = "p2p_tc.cu" if tensor_contraction else "p2p_f32.cu"
+    ksrc = acct["source"]
     traffic = recorded_traffic(ksrc, w.name) if args.precision != "fp64" else None
 
     solve = None
@@ -467,14 +489,13 @@ def run_ours(args):
             "e2e": {"value": job_throughput(world, N, R, e2e_t), "unit": UNIT, "h2d_bytes_per_step": int(xh.numel() * 8),
                     "d2h_bytes_per_step": int(yh.numel() * 8)},
             "gpu_launches": int(launches),
-            "roofline": {"kernel": ("p2p (near field): k_sum_tc, kernel evaluation on the FP32 pipe, "
-                                    "contraction on tcgen05 TF32 (counted separately below)") if tensor_contraction
-                         else "p2p (near field): k_sum_f32",
+            "roofline": {"kernel": acct["kernel"], "near_engine": engine,
                          "bound": "alu", "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
-                         "flops_per_pair": flops_pair, "pairs_per_launch": pairs,
-                         "tensor_flops_per_pair": (3 * 2 * 16) if tensor_contraction else 0,
-                         "tensor_tflops": (pairs * 96 / (p2p_avg_ms / 1e3) / 1e12) if tensor_contraction else 0.0,
+                         "flops_per_eval": acct["flops_per_eval"], "evals_per_launch": acct["evals"],
+                         "ordered_pairs_per_launch": pairs,
+                         "tensor_flops_per_ordered_pair": (3 * 2 * 16) if acct["tensor"] else 0,
+                         "tensor_tflops": (pairs * 96 / (p2p_avg_ms / 1e3) / 1e12) if acct["tensor"] else 0.0,
                          "launch_ms": p2p_avg_ms,
                          "traffic_basis": traffic_basis(ksrc, w.name) if args.precision != "fp64" else None,
                          "peak_basis": f"{sms} SMs x {FP32_LANES} FP32 lanes x 2 flop x {clock_mhz:.0f} MHz "
@@ -578,6 +599,76 @@ def run_solve_sample(args):
                                           **_serve_poisson(sweep, "mixed", 1e-2)}}
 
 
+def run_eta_sweep(args):
+    """The bench workload (d = 10 Gaussian, N = 2^20, 16 RHS, mixed) with the
+    Sec. 6.2 weight rule at eta = 0.5 (the paper's value) and eta = 1:
+    |Lambda|, far blocks, near pairs, matvec time (CUDA events, L2 flushed)
+    and the compression error of the mixed matvec against the exact product
+    on sampled rows (float64 evaluation of K[rows, :] x)."""
+    import numpy as np
+    import torch
+    import __graft_entry__ as ge
+    ge.build()
+    import dwfmm_inputs as di
+    from paper_2402_09531_gb300 import Plan
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    w = workload("mixed")
+    if args.n:
+        w = di.scaled(w, args.n)
+    X, f = di.sites_and_rhs(w)
+    Xd = torch.from_numpy(X).to(dev)
+    xd = torch.from_numpy(f).to(dev)
+    rows = np.sort(np.random.default_rng(11).choice(w.n, size=min(1024, w.n), replace=False))
+    # exact K[rows, :] x by float64 evaluation at the sampled sites
+    pex = Plan(d=w.d, kernel=w.kernel, sigma=w.sigma, gamma=w.gamma, q=1.0, eta=1.0, leaf_size=w.leaf,
+               precision="fp64", max_rhs=w.nrhs)
+    pex.tree_build(Xd)
+    exact = torch.zeros((w.nrhs, len(rows)), dtype=torch.float64, device=dev)
+    pex.evaluate(torch.from_numpy(np.ascontiguousarray(X[rows])).to(dev), xd, exact)
+    torch.cuda.synchronize()
+    pex.close()
+    exact = exact.cpu().numpy()
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    out = {"workload": w.name, "weights": "Sec. 6.2 rule (tau_k^-1 = eta b_k, b_k = 2 gamma_k)",
+           "rows_sampled": int(len(rows)), "etas": {}}
+    for eta in (0.5, 1.0):
+        plan = Plan(d=w.d, kernel=w.kernel, sigma=w.sigma, gamma=w.gamma, weight_rule="paper_logrho", q=w.q,
+                    eta=eta, leaf_size=w.leaf, precision="mixed", max_rhs=w.nrhs)
+        plan.tree_build(Xd)
+        n_x, n_far, n_near, depth = plan.info()
+        pairs, diag = near_pairs(plan)
+        yd = torch.empty_like(xd)
+        for _ in range(2):
+            plan.matvec(xd, yd)
+        torch.cuda.synchronize()
+        times = []
+        for _ in range(3):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            plan.matvec(xd, yd)
+            b.record(stream)
+            torch.cuda.synchronize()
+            times.append(a.elapsed_time(b))
+        plan.set_profiling(True, serialize=True)
+        plan.matvec(xd, yd)
+        iso = plan.phase_times(reset=True)
+        plan.set_profiling(False)
+        y = yd.cpu().numpy()[:, rows]
+        col = np.linalg.norm(y - exact, axis=1) / np.linalg.norm(exact, axis=1)
+        out["etas"][str(eta)] = {
+            "n_x": n_x, "far_blocks": n_far, "near_blocks": n_near, "depth": depth,
+            "near_pairs": pairs, "near_fraction": pairs / float(w.n) ** 2, "near_engine": plan.near_engine(),
+            "matvec_ms": statistics.mean(times), "phase_ms_isolated": {k: v[0] for k, v in iso.items()},
+            "throughput_pts_rhs_per_s": w.n * w.nrhs / (statistics.mean(times) / 1e3),
+            "compression_error_worst_column": float(col.max()),
+            "compression_error_block": float(np.linalg.norm(y - exact) / np.linalg.norm(exact))}
+        plan.close()
+    print(json.dumps(out), flush=True)
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -618,12 +709,16 @@ def main():
     ap.add_argument("--sweep-requests", type=int, default=32)
     ap.add_argument("--sweep-nmax", type=int, default=3000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--eta-sweep", action="store_true",
+                    help="the bench workload with the Sec. 6.2 weights at eta = 0.5 and 1 (own JSON line)")
     ap.add_argument("--oracle-sample", default=None)
     args = ap.parse_args()
     if args.oracle_sample:
         print(json.dumps(oracle_sample(args.oracle_sample, args.steps, args.warmup)), flush=True)
         return
-    if args.impl == "reference":
+    if args.eta_sweep:
+        run_eta_sweep(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

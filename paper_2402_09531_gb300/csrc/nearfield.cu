@@ -263,19 +263,21 @@ __global__ void k_sym_fill(const int32_t* rowptr, const int32_t* col, int L, con
 }
 
 // Slot of the lower entry (X, T < X): the position of (T, X) in the upper
-// list; a missing one means the near relation is not symmetric.
+// list (each upper row is sorted by source, so a binary search finds it); a
+// missing one means the near relation is not symmetric.
 __global__ void k_sym_slots(const int32_t* lorow, const int32_t* lo_src, const int32_t* uprow, const int32_t* up_s,
                             int L, int32_t* lo_slot, int* bad) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= L) return;
   for (int k = lorow[x]; k < lorow[x + 1]; ++k) {
     const int t = lo_src[k];
-    int slot = -1;
-    for (int e = uprow[t]; e < uprow[t + 1]; ++e)
-      if (up_s[e] == x) {
-        slot = e;
-        break;
-      }
+    int a = uprow[t], b = uprow[t + 1];   // first entry with up_s >= x in [a, b)
+    while (a < b) {
+      const int m = (a + b) >> 1;
+      if (up_s[m] < x) a = m + 1;
+      else b = m;
+    }
+    const int slot = (a < uprow[t + 1] && up_s[a] == x) ? a : -1;
     if (slot < 0) atomicExch(bad, 1);
     lo_slot[k] = slot < 0 ? 0 : slot;
   }

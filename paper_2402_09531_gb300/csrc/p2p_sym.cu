@@ -10,8 +10,8 @@
 // kernel constant folded in): the CUDA cores evaluate E' = 2^(2 x'.s'), the
 // point factors sit on the charges and on the finished sums.
 //
-// Arithmetic.  E' is split into FP16 hi + lo (hi = E' rounded to FP16, lo =
-// the FP16 rounding of E' - hi); the charges q' = q * factor, normalised per
+// Arithmetic.  E' is split into FP16 hi + lo (hi = E' truncated to the FP16
+// significand, lo = the FP16 rounding of E' - hi); the charges q' = q * factor, normalised per
 // right-hand side by a power of two so that |q'| <= 1, are split the same
 // way.  tcgen05.mma.kind::f16 (FP32 accumulation) forms hi*hi + hi*lo +
 // lo*hi, 11-bit significands on both sides like the TF32 split.  The
@@ -103,6 +103,21 @@ __device__ __forceinline__ float phi_sym(float a) {
   return fmaf(r, e, e);
 }
 
+// Two values -> packed FP16 hi and lo.  hi keeps the top 10 stored mantissa
+// bits of each value (exactly an FP16 number inside its normal range, where
+// E' stays), lo = value - hi is exact in FP32 and rounded to FP16 once: the
+// pair carries ~2^-22 relative.
+__device__ __forceinline__ void split_f16x2(float e0, float e1, uint32_t& hi, uint32_t& lo) {
+  const float h0 = __uint_as_float(__float_as_uint(e0) & 0xFFFFE000u);
+  const float h1 = __uint_as_float(__float_as_uint(e1) & 0xFFFFE000u);
+  float l0, l1;
+  up(sub2(pk(e0, e1), pk(h0, h1)), l0, l1);
+  const __half2 h = __floats2half2_rn(h0, h1);
+  const __half2 l = __floats2half2_rn(l0, l1);
+  hi = *reinterpret_cast<const uint32_t*>(&h);
+  lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+
 // E' for two targets (A, B) and sources j..j+7 of the stage (row stride 64
 // floats); results as FP16 hi / lo rows (4 words each).
 template <int D, int KER>
@@ -146,27 +161,9 @@ __device__ __forceinline__ void eval8x2(const float* sc, int j, const u64* xa, c
   for (int u = 0; u < 4; ++u) {
     float f0, f1;
     up(pa[u], f0, f1);
-    {
-      const float e0 = phi_sym<KER>(f0), e1 = phi_sym<KER>(f1);
-      const __half2 h = __floats2half2_rn(e0, e1);
-      const float2 hf = __half22float2(h);
-      float l0, l1;
-      up(sub2(pk(e0, e1), pk(hf.x, hf.y)), l0, l1);
-      const __half2 l = __floats2half2_rn(l0, l1);
-      ha[u] = *reinterpret_cast<const uint32_t*>(&h);
-      la[u] = *reinterpret_cast<const uint32_t*>(&l);
-    }
+    split_f16x2(phi_sym<KER>(f0), phi_sym<KER>(f1), ha[u], la[u]);
     up(pb[u], f0, f1);
-    {
-      const float e0 = phi_sym<KER>(f0), e1 = phi_sym<KER>(f1);
-      const __half2 h = __floats2half2_rn(e0, e1);
-      const float2 hf = __half22float2(h);
-      float l0, l1;
-      up(sub2(pk(e0, e1), pk(hf.x, hf.y)), l0, l1);
-      const __half2 l = __floats2half2_rn(l0, l1);
-      hb[u] = *reinterpret_cast<const uint32_t*>(&h);
-      lb[u] = *reinterpret_cast<const uint32_t*>(&l);
-    }
+    split_f16x2(phi_sym<KER>(f0), phi_sym<KER>(f1), hb[u], lb[u]);
   }
 }
 
