@@ -262,6 +262,13 @@ def p2p_accounting(engine: str, pairs: int, diag: int, d: int, R: int):
     multiply-adds, ~4 for phi) and where the 2R flops per ordered pair of the
     contraction run.  The symmetric engine evaluates each unordered pair of
     sites once: (pairs + diag) / 2 evaluations."""
+    if engine == "mixed_symmetric_fp16_tensor_exponent":
+        return {"evals": (pairs + diag) // 2, "flops_per_eval": 3 * d + 4, "tensor": True,
+                "source": "p2p_sym.cu",
+                "kernel": ("p2p (near field): k_near_sym_gtc, each unordered near pair of sites evaluated once: "
+                           "the exponent 2x'.s' (2d flops) and both contractions on tcgen05 FP16 hi/lo, exp2 and "
+                           "the FP16 split on the CUDA cores; the 3d + 4 flops of the evaluation are counted "
+                           "against the FP32 peak, the tensor-pipe flops beside them")}
     if engine == "mixed_symmetric_fp16_tensor":
         return {"evals": (pairs + diag) // 2, "flops_per_eval": 3 * d + 4, "tensor": True,
                 "source": "p2p_sym.cu",
@@ -517,27 +524,30 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def _serve(reqs, precision, lam):
+def _serve(reqs, precision, lam, batched=False):
     from paper_2402_09531_gb300.serving import Request, Server, summarize
     rs = [Request(rid=r.rid, X=r.X, f=r.f, kernel=r.kernel, gamma=r.gamma, q=r.q, eta=r.eta, leaf=r.leaf,
                   weight_rule=r.weight_rule, lam=lam, rtol=r.rtol, maxit=r.maxit) for r in reqs]
-    srv = Server(precision=precision, max_active=8)
+    srv = Server(precision=precision, max_active=8, batched=batched)
     srv.run(rs[:1])                                     # warm-up (plan pool, kernel attributes)
+    srv.batch_rebuilds = 0
     t0 = time.perf_counter()
     res = srv.run(rs)
     out = summarize(res, time.perf_counter() - t0)
-    out.update({"precision": precision, "lambda": lam, "peak_active": srv.peak_active})
+    out.update({"precision": precision, "lambda": lam, "peak_active": srv.peak_active, "batched": batched})
+    if batched:
+        out["batch_rebuilds"] = srv.batch_rebuilds
     srv.close()
     return out
 
 
-def _serve_poisson(reqs, precision, lam, loads=(0.5, 0.8, 1.0), seed=7):
+def _serve_poisson(reqs, precision, lam, loads=(0.5, 0.8, 1.0), seed=7, batched=False):
     """Offered-load sweep: the closed-loop rate (all requests at t=0) sets the
     scale; then Poisson arrivals at each fraction of it (seeded exponential
     gaps), p50/p99 latency measured from each request's arrival."""
     import numpy as np
     from paper_2402_09531_gb300.serving import Request, Server, summarize
-    base = _serve(reqs, precision, lam)
+    base = _serve(reqs, precision, lam, batched=batched)
     rate = base["solves_per_s"]
     rng = np.random.default_rng(seed)
     out = {"closed_loop_solves_per_s": rate, "requests": len(reqs)}
@@ -547,7 +557,7 @@ def _serve_poisson(reqs, precision, lam, loads=(0.5, 0.8, 1.0), seed=7):
         rs = [Request(rid=r.rid, X=r.X, f=r.f, kernel=r.kernel, gamma=r.gamma, q=r.q, eta=r.eta, leaf=r.leaf,
                       weight_rule=r.weight_rule, lam=lam, rtol=r.rtol, maxit=r.maxit, arrival=float(a))
               for r, a in zip(reqs, arrival)]
-        srv = Server(precision=precision, max_active=8)
+        srv = Server(precision=precision, max_active=8, batched=batched)
         srv.run([dataclasses.replace(rs[0], rid=-1, arrival=0.0)])   # warm-up (plan pool)
         t0 = time.perf_counter()
         res = srv.run(rs)
@@ -594,9 +604,13 @@ def run_solve_sample(args):
             "fp64_lambda_1e-6": _serve(reqs, "fp64", 1e-6),
             "fp64_lambda_1e-2": _serve(reqs, "fp64", 1e-2),
             "mixed_lambda_1e-2": _serve(reqs, "mixed", 1e-2),
+            "mixed_lambda_1e-2_batched": _serve(reqs, "mixed", 1e-2, batched=True),
             "mixed_lambda_1e-2_poisson": {"n_range": [min(r.X.shape[0] for r in sweep),
                                                       max(r.X.shape[0] for r in sweep)],
-                                          **_serve_poisson(sweep, "mixed", 1e-2)}}
+                                          **_serve_poisson(sweep, "mixed", 1e-2)},
+            "mixed_lambda_1e-2_poisson_batched": {"n_range": [min(r.X.shape[0] for r in sweep),
+                                                              max(r.X.shape[0] for r in sweep)],
+                                                  **_serve_poisson(sweep, "mixed", 1e-2, batched=True)}}
 
 
 def run_eta_sweep(args):
@@ -669,6 +683,130 @@ def run_eta_sweep(args):
     print(json.dumps(out), flush=True)
 
 
+def run_cfg2_solve(args):
+    """CG solve of (K_tilde + 1e-6 I) c = f on the float64 d = 8 Matern
+    workload (N = 262144, rtol 1e-8): the time per iteration at full size
+    (blocking solve capped at a few iterations) and the iteration counts of
+    solves of the same shape at smaller N (capped), from which the full solve
+    is extrapolated (stated as such).  One JSON line per measurement, as it
+    completes."""
+    import numpy as np
+    import torch
+    import __graft_entry__ as ge
+    ge.build()
+    import dwfmm_inputs as di
+    from paper_2402_09531_gb300 import Plan
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    base = workload("fp64")
+
+    def solve(w, maxit):
+        X, f = di.sites_and_rhs(w)
+        plan = Plan(d=w.d, kernel=w.kernel, sigma=w.sigma, gamma=w.gamma, q=w.q, eta=w.eta, leaf_size=w.leaf,
+                    precision="fp64", max_rhs=1)
+        plan.tree_build(torch.from_numpy(X).to(dev))
+        fd = torch.from_numpy(f).to(dev)
+        cd = torch.zeros_like(fd)
+        plan.solve(w.lam, fd, cd, rtol=w.rtol, maxit=2)           # warm-up (workspace)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        st, its, rel = plan.solve(w.lam, fd, cd, rtol=w.rtol, maxit=maxit)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t
+        plan.close()
+        return {"n": w.n, "status": int(st), "iters": int(its), "relres": float(rel[0]), "s": dt,
+                "ms_per_iter": dt * 1e3 / max(1, its)}
+
+    full = solve(base, 20)
+    print(json.dumps({"workload": base.name, "lambda": base.lam, "rtol": base.rtol, "full_size": full}), flush=True)
+    done = []
+    for n in args.cfg2_sizes:
+        r = solve(di.scaled(base, n), args.cfg2_maxit)
+        print(json.dumps({"size": r}), flush=True)
+        if r["status"] == 0:
+            done.append((n, r["iters"]))
+    if len(done) >= 2:
+        ns, its = np.array([a for a, _ in done], dtype=float), np.array([b for _, b in done], dtype=float)
+        slope, icpt = np.polyfit(np.log(ns), np.log(its), 1)
+        it_full = float(np.exp(icpt) * base.n ** slope)
+        print(json.dumps({"extrapolated": {"iterations": it_full, "fit": f"iters ~ N^{slope:.3f}",
+                                           "solve_s": it_full * full["ms_per_iter"] / 1e3,
+                                           "note": "power law in N through the converged smaller solves, times "
+                                                   "the measured full-size time per iteration"}}), flush=True)
+
+
+def run_batch(args):
+    """The batching workload: 256 independent problems (N log-uniform in
+    [2048, 65536], d in {6..12}, gamma_k = k^-2, Matern-3/2, q = 5, 1-8
+    right-hand sides, float32) as one fused batch matvec under a captured
+    graph, against the same problems' matvecs one after another.  Throughput
+    is sum_p N_p R_p per second; L2 flushed between steps."""
+    import torch
+    import __graft_entry__ as ge
+    ge.build()
+    import dwfmm_inputs as di
+    from paper_2402_09531_gb300 import Batch, Plan
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    probs = di.batching_problems(args.batch_count)
+    plans, xs, ys = [], [], []
+    t0 = time.perf_counter()
+    for w in probs:
+        X, f = di.sites_and_rhs(w)
+        p = Plan(d=w.d, kernel=w.kernel, gamma=w.gamma, q=w.q, eta=w.eta, leaf_size=w.leaf,
+                 precision=args.precision if args.precision != "fp64" else "fp32", max_rhs=w.nrhs)
+        p.tree_build(torch.from_numpy(X).to(dev))
+        plans.append(p)
+        xs.append(torch.from_numpy(f).to(dev))
+        ys.append(torch.empty_like(xs[-1]))
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    b = Batch(plans, [w.nrhs for w in probs])
+    torch.cuda.synchronize()
+    create_s = time.perf_counter() - t0
+    units = sum(w.n * w.nrhs for w in probs)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn, steps):
+        for _ in range(max(3, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        out = []
+        for _ in range(steps):
+            flush.zero_()
+            a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            z.record(stream)
+            torch.cuda.synchronize()
+            out.append(a.elapsed_time(z))
+        return statistics.mean(out)
+
+    ms_batch = timed(lambda: b.matvec(xs, ys), args.steps)
+
+    def one_by_one():
+        for p, x, y in zip(plans, xs, ys):
+            p.matvec(x, y)
+    ms_seq = timed(one_by_one, max(2, args.steps // 2))
+    info = b.info()
+    print(json.dumps({
+        "workload": f"batching: {len(probs)} problems, N log-uniform in [2048, 65536], d in {{6..12}}, "
+                    f"gamma_k = k^-2, Matern-3/2, q = 5, 1-8 RHS, leaf 128",
+        "precision": args.precision if args.precision != "fp64" else "fp32",
+        "problems": len(probs), "sites": sum(w.n for w in probs), "pts_rhs_per_step": units,
+        "batch_ms": ms_batch, "batch_pts_rhs_per_s": units / (ms_batch / 1e3),
+        "sequential_ms": ms_seq, "sequential_pts_rhs_per_s": units / (ms_seq / 1e3),
+        "speedup": ms_seq / ms_batch, "tree_builds_s": build_s, "batch_create_s": create_s,
+        "launch_shape": "one launch per right-hand-side class" if info["split"] else "one padded launch",
+        "autotune_ms": info["tune_ms"], "leaves": info["leaves"],
+        "l2": "flushed between steps (512 MiB write)"}), flush=True)
+    b.close()
+    for p in plans:
+        p.close()
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -709,6 +847,13 @@ def main():
     ap.add_argument("--sweep-requests", type=int, default=32)
     ap.add_argument("--sweep-nmax", type=int, default=3000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch", action="store_true",
+                    help="the 256-problem batching workload: fused batch matvec against one matvec per problem")
+    ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--cfg2-solve", action="store_true",
+                    help="float64 CG solve of the d = 8 Matern workload: per-iteration time, extrapolation")
+    ap.add_argument("--cfg2-sizes", type=int, nargs="*", default=[2048, 4096, 8192, 16384])
+    ap.add_argument("--cfg2-maxit", type=int, default=10000)
     ap.add_argument("--eta-sweep", action="store_true",
                     help="the bench workload with the Sec. 6.2 weights at eta = 0.5 and 1 (own JSON line)")
     ap.add_argument("--oracle-sample", default=None)
@@ -718,6 +863,10 @@ def main():
         return
     if args.eta_sweep:
         run_eta_sweep(args)
+    elif args.cfg2_solve:
+        run_cfg2_solve(args)
+    elif args.batch:
+        run_batch(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -271,6 +271,20 @@ dwfmm_status dwfmm_batch_create(const dwfmm_plan* plans, const int32_t* nrhs, in
                                 dwfmm_batch* out);
 dwfmm_status dwfmm_batch_matvec(dwfmm_batch batch, const double* const* x, double* const* y, void* stream);
 dwfmm_status dwfmm_batch_info(dwfmm_batch batch, int32_t* split, double* tune_ms, int64_t* leaves);
+
+/* Batched CG (Sec. 2, Eq. (2.2); the CG of Sec. 6.2): `iters` iterations of
+ * the incremental CG of every problem of the batch, each begun with
+ * dwfmm_cg_begin on its plan (its own lambda, right-hand sides and rtol,
+ * nrhs equal to the problem's batch nrhs).  Every iteration computes
+ * Ap = K_tilde p of all problems as one fused batch matvec and updates all
+ * problems' vectors with fused kernels; the per-column decisions are those of
+ * dwfmm_cg_step (a column stops on convergence or breakdown, the others go
+ * on).  Enqueued on `stream`; afterwards each plan's dwfmm_cg_poll and
+ * dwfmm_cg_result read its state as after dwfmm_cg_step.  Inner products use
+ * a fixed partition, so the result does not depend on timing.  Errors:
+ * DWFMM_ERR_STATE if a plan has no CG begun, DWFMM_ERR_INVALID_ARG if its
+ * right-hand-side count differs from the batch's. */
+dwfmm_status dwfmm_batch_cg_step(dwfmm_batch batch, int32_t iters, void* stream);
 dwfmm_status dwfmm_batch_destroy(dwfmm_batch batch);
 
 /* Release every resource of the plan (NULL is accepted).  Synchronises the
@@ -293,7 +307,8 @@ dwfmm_status dwfmm_plan_info(dwfmm_plan plan, int64_t* n_x, int64_t* n_far, int6
  * over its near list; 1 float64, each unordered near pair of leaves once;
  * 2 float32 on the CUDA cores; 3 MIXED, contraction on the tensor cores (TF32
  * hi/lo, every ordered pair); 4 MIXED, each unordered near pair once, FP16
- * hi/lo on the tensor cores with fixed-point transposed sums. */
+ * hi/lo on the tensor cores with fixed-point transposed sums; 5 as 4, with
+ * the Gaussian's exponent 2x'.s' also on the tensor cores. */
 dwfmm_status dwfmm_near_engine(dwfmm_plan plan, int32_t* engine);
 
 /* Copy out plan data (host buffers, NULL to skip), for tests and tools:

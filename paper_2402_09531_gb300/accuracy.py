@@ -184,6 +184,8 @@ def main():
     ap.add_argument("--lambdas", type=int, default=3)
     ap.add_argument("--repeats", type=int, default=1)
     ap.add_argument("--precision", default="fp32")
+    ap.add_argument("--leaf", type=int, default=128)
+    ap.add_argument("--maxit", type=int, default=20000)
     ap.add_argument("--ce-only", action="store_true", help="compression error over the sigma grid only")
     ap.add_argument("--pe-at", default=None,
                     help="prediction error at comma-separated sigma:lambda points instead of the grid")
@@ -191,10 +193,10 @@ def main():
     if args.pe_at:
         pts = [tuple(float(v) for v in p.split(":")) for p in args.pe_at.split(",")]
         res = prediction_points(n=args.n, d=20, r=args.r, points=pts, repeats=args.repeats,
-                                precision=args.precision)
+                                precision=args.precision, leaf=args.leaf, maxit=args.maxit)
     else:
         res = study(n=args.n, r=args.r, n_sigma=args.sigmas, n_lambda=args.lambdas, repeats=args.repeats,
-                    precision=args.precision, pe=not args.ce_only)
+                    precision=args.precision, pe=not args.ce_only, leaf=args.leaf, maxit=args.maxit)
     print(json.dumps(res))
 
 

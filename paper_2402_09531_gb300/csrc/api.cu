@@ -79,6 +79,9 @@ void Plan::free_tree() {
   sym_fwd.release();
   sym_acc.release();
   sym_colmax.release();
+  sym_xa16.release();
+  sym_xb16.release();
+  sym_x16_ok = false;
   dpad = -1;
 }
 
@@ -717,6 +720,14 @@ dwfmm_status dwfmm_batch_matvec(dwfmm_batch batch, const double* const* x, doubl
   if (!batch || !x || !y) return DWFMM_ERR_INVALID_ARG;
   return guarded(nullptr, [&]() -> dwfmm_status {
     dw::batch_matvec(*batch->B, x, y, static_cast<cudaStream_t>(stream));
+    return DWFMM_OK;
+  });
+}
+
+dwfmm_status dwfmm_batch_cg_step(dwfmm_batch batch, int32_t iters, void* stream) {
+  if (!batch) return DWFMM_ERR_INVALID_ARG;
+  return guarded(nullptr, [&]() -> dwfmm_status {
+    dw::batch_cg_step(*batch->B, iters, static_cast<cudaStream_t>(stream));
     return DWFMM_OK;
   });
 }

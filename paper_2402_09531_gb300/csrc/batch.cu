@@ -13,6 +13,7 @@
 // padded to the largest class and as one launch per class, and the faster
 // shape is captured.
 #include <algorithm>
+#include <cstring>
 #include <numeric>
 #include <vector>
 
@@ -44,10 +45,29 @@ struct Batch {
   cudaStream_t stream = nullptr, side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_copy = nullptr;
   bool copied = false;
+  DBuf<char> cg_tab;     // batched CG: problem, segment and block tables
+  DBuf<double> cg_part;  // batched CG: partial inner products
+  std::vector<char> cg_host;     // content of cg_tab (uploaded only when it changes)
+  char* cg_pinned = nullptr;     // pinned staging of the upload
+  size_t cg_pinned_n = 0;
+  cudaEvent_t cg_ev = nullptr;   // the last upload is done
+  bool cg_copied = false;
+  cudaGraph_t cg_graph = nullptr;        // `cg_iters` batched CG iterations
+  cudaGraphExec_t cg_exec = nullptr;
+  int cg_iters = -1, cg_nseg = -1, cg_nblk = -1;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
 
   void release() {
+    if (cg_exec) cudaGraphExecDestroy(cg_exec);
+    if (cg_graph) cudaGraphDestroy(cg_graph);
+    if (cg_pinned) cudaFreeHost(cg_pinned);
+    if (cg_ev) cudaEventDestroy(cg_ev);
+    cg_exec = nullptr;
+    cg_graph = nullptr;
+    cg_pinned = nullptr;
+    cg_pinned_n = 0;
+    cg_ev = nullptr;
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
     if (h_probs) cudaFreeHost(h_probs);
@@ -401,6 +421,225 @@ void batch_info(const Batch& B, int32_t* split, double* tune_ms, int64_t* leaves
     tune_ms[1] = B.tune_ms[1];
   }
   if (leaves) *leaves = B.Ltot;
+}
+
+}  // namespace dw
+
+// ---------------------------------------------------------------------------
+// Batched CG: one iteration advances the incremental CG (dwfmm_cg_begin) of
+// every problem of the batch.  Ap = K_tilde p of all problems is the batch's
+// fused matvec (its captured graph); the shift, the inner products, the
+// x / r / p updates and the per-column scalar decisions (the same as the
+// single-plan iteration: breakdown on pAp = 0 or not finite, convergence on
+// ||r||^2 <= rtol^2 ||f||^2) are fused kernels over all problems.  Inner
+// products are computed in a fixed partition (block partials, then their
+// sum in block order), so results do not depend on timing.
+// ---------------------------------------------------------------------------
+
+namespace dw {
+
+namespace {
+
+constexpr int kBcgThreads = 256;
+constexpr int64_t kBcgPerBlock = 8192;   // elements of one column per partial block
+
+struct BcgSeg {   // one (problem, column): its partial blocks
+  int item, col, first, nblk;
+};
+
+// Partial inner products of every (problem, column).  mode 0: ap += lam p and
+// partial sum of p . ap; mode 1: c += alpha p, r -= alpha ap and partial sum
+// of r . r (alpha = coef).
+__global__ void k_bcg_partial(const CgPtrs* items, const BcgSeg* segs, const int2* blk, int mode, double* part) {
+  __shared__ double sh[kBcgThreads / 32];
+  const int2 bs = blk[blockIdx.x];                 // (segment, block within it)
+  const BcgSeg g = segs[bs.x];
+  const CgPtrs it = items[g.item];
+  const int64_t n = it.n;
+  const int64_t lo = static_cast<int64_t>(bs.y) * kBcgPerBlock;
+  const int64_t hi = lo + kBcgPerBlock < n ? lo + kBcgPerBlock : n;
+  const int64_t off = static_cast<int64_t>(g.col) * n;
+  double acc = 0.0;
+  if (mode == 0) {
+    for (int64_t i = lo + threadIdx.x; i < hi; i += kBcgThreads) {
+      const double pv = it.p[off + i];
+      const double v = it.ap[off + i] + it.lam * pv;
+      it.ap[off + i] = v;
+      acc += pv * v;
+    }
+  } else {
+    const double a = it.coef[g.col];
+    for (int64_t i = lo + threadIdx.x; i < hi; i += kBcgThreads) {
+      it.c[off + i] += a * it.p[off + i];
+      const double rv = it.r[off + i] - a * it.ap[off + i];
+      it.r[off + i] = rv;
+      acc += rv * rv;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kBcgThreads / 32; ++w) t += sh[w];
+    part[blockIdx.x] = t;
+  }
+}
+
+// Per (problem, column): the inner product from its partials in block
+// order, then the scalar step.  mode 0: alpha = rr / pAp; mode 1: the new
+// rr, convergence, beta.
+__global__ void k_bcg_scalar(const CgPtrs* items, const BcgSeg* segs, int nseg, int mode, const double* part) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nseg) return;
+  const BcgSeg g = segs[k];
+  const CgPtrs it = items[g.item];
+  double v = 0.0;
+  for (int b = 0; b < g.nblk; ++b) v += part[g.first + b];
+  const int r = g.col;
+  if (mode == 0) {
+    double a = 0.0;
+    if (it.status[r] == 0) {
+      if (v == 0.0 || !isfinite(v)) it.status[r] = 2;
+      else a = it.rr[r] / v;
+    }
+    it.pap[r] = v;
+    it.coef[r] = a;
+  } else {
+    double b = 0.0;
+    if (it.status[r] == 0) {
+      it.iters[r] += 1;
+      if (v <= *it.rtol2 * it.bn2[r]) it.status[r] = 1;
+      b = v / it.rr[r];
+      it.rr[r] = v;
+    }
+    it.tmp[r] = v;
+    it.coef[r] = b;
+  }
+}
+
+// p = r + beta p for every problem and column.
+__global__ void k_bcg_p(const CgPtrs* items, const BcgSeg* segs, const int2* blk) {
+  const int2 bs = blk[blockIdx.x];
+  const BcgSeg g = segs[bs.x];
+  const CgPtrs it = items[g.item];
+  const int64_t n = it.n;
+  const int64_t lo = static_cast<int64_t>(bs.y) * kBcgPerBlock;
+  const int64_t hi = lo + kBcgPerBlock < n ? lo + kBcgPerBlock : n;
+  const int64_t off = static_cast<int64_t>(g.col) * n;
+  const double b = it.coef[g.col];
+  for (int64_t i = lo + threadIdx.x; i < hi; i += kBcgThreads) it.p[off + i] = it.r[off + i] + b * it.p[off + i];
+}
+
+}  // namespace
+
+void batch_cg_step(Batch& B, int iters, cudaStream_t s) {
+  if (iters < 0) fail(DWFMM_ERR_INVALID_ARG, "iters must be >= 0");
+  std::vector<CgPtrs> items(B.P);
+  std::vector<const double*> xs(B.P);
+  std::vector<double*> ys(B.P);
+  std::vector<BcgSeg> segs;
+  std::vector<int2> blk;
+  for (int i = 0; i < B.P; ++i) {
+    Plan& P = *B.plans[i];
+    if (!P.cgs.active || !P.cg_p.p) fail(DWFMM_ERR_STATE, "every plan of the batch needs dwfmm_cg_begin first");
+    if (P.cgs.R != B.R[i]) fail(DWFMM_ERR_INVALID_ARG, "a plan's CG right-hand sides differ from its batch nrhs");
+    items[i] = cg_ptrs(P);
+    const int c = B.order[i];
+    xs[c] = P.cg_p.p;
+    ys[c] = P.cg_ap.p;
+    const int nb = static_cast<int>((P.N + kBcgPerBlock - 1) / kBcgPerBlock);
+    for (int r = 0; r < B.R[i]; ++r) {
+      const int seg = static_cast<int>(segs.size());
+      segs.push_back(BcgSeg{i, r, static_cast<int>(blk.size()), nb});
+      for (int b = 0; b < nb; ++b) blk.push_back(make_int2(seg, b));
+    }
+  }
+  // device tables: uploaded on the stream only when their content changed
+  // (a pinned staging buffer, reused once its previous copy is done)
+  const size_t bi = sizeof(CgPtrs) * items.size(), bs = sizeof(BcgSeg) * segs.size(), bb = sizeof(int2) * blk.size();
+  std::vector<char> host(bi + bs + bb);
+  std::memcpy(host.data(), items.data(), bi);
+  std::memcpy(host.data() + bi, segs.data(), bs);
+  std::memcpy(host.data() + bi + bs, blk.data(), bb);
+  const int nseg = static_cast<int>(segs.size()), nblk = static_cast<int>(blk.size());
+  if (host != B.cg_host) {
+    if (B.cg_copied) DW_CUDA(cudaEventSynchronize(B.cg_ev));
+    if (B.cg_pinned_n < host.size()) {
+      if (B.cg_pinned) cudaFreeHost(B.cg_pinned);
+      B.cg_pinned = nullptr;
+      B.cg_pinned_n = 0;
+      DW_CUDA(cudaMallocHost(reinterpret_cast<void**>(&B.cg_pinned), host.size()));
+      B.cg_pinned_n = host.size();
+    }
+    if (!B.cg_ev) DW_CUDA(cudaEventCreateWithFlags(&B.cg_ev, cudaEventDisableTiming));
+    const bool grow = B.cg_tab.n < host.size() || B.cg_part.n < blk.size();
+    if (grow && B.cg_exec) {   // the captured iterations point at the old tables
+      cudaGraphExecDestroy(B.cg_exec);
+      cudaGraphDestroy(B.cg_graph);
+      B.cg_exec = nullptr;
+      B.cg_graph = nullptr;
+    }
+    B.cg_tab.alloc(host.size());
+    B.cg_part.alloc(blk.size());
+    std::memcpy(B.cg_pinned, host.data(), host.size());
+    DW_CUDA(cudaMemcpyAsync(B.cg_tab.p, B.cg_pinned, host.size(), cudaMemcpyHostToDevice, s));
+    DW_CUDA(cudaEventRecord(B.cg_ev, s));
+    B.cg_copied = true;
+    B.cg_host.swap(host);
+    // the matvec's problem table (x = p, y = Ap of every problem)
+    if (B.copied) DW_CUDA(cudaEventSynchronize(B.ev_copy));
+    for (int i = 0; i < B.P; ++i) {
+      const int c = B.order[i];
+      B.h_probs[i].x = xs[c];
+      B.h_probs[i].y = ys[c];
+    }
+    DW_CUDA(cudaMemcpyAsync(B.probs.p, B.h_probs, sizeof(ProbF32) * B.P, cudaMemcpyHostToDevice, s));
+    DW_CUDA(cudaEventRecord(B.ev_copy, s));
+    B.copied = true;
+  }
+  const CgPtrs* d_items = reinterpret_cast<const CgPtrs*>(B.cg_tab.p);
+  const BcgSeg* d_segs = reinterpret_cast<const BcgSeg*>(B.cg_tab.p + bi);
+  const int2* d_blk = reinterpret_cast<const int2*>(B.cg_tab.p + bi + bs);
+  // `iters` iterations captured once per (iteration count, table shape) on the
+  // batch's stream and replayed on the caller's
+  if (iters > 0 && (!B.cg_exec || B.cg_iters != iters || B.cg_nseg != nseg || B.cg_nblk != nblk)) {
+    if (B.cg_exec) cudaGraphExecDestroy(B.cg_exec);
+    if (B.cg_graph) cudaGraphDestroy(B.cg_graph);
+    B.cg_exec = nullptr;
+    B.cg_graph = nullptr;
+    cudaStream_t bst = B.stream;
+    DW_CUDA(cudaStreamBeginCapture(bst, cudaStreamCaptureModeThreadLocal));
+    for (int k = 0; k < iters; ++k) {
+      enqueue_matvec(B);
+      k_bcg_partial<<<nblk, kBcgThreads, 0, bst>>>(d_items, d_segs, d_blk, 0, B.cg_part.p);
+      k_bcg_scalar<<<ceil_div(nseg, 64), 64, 0, bst>>>(d_items, d_segs, nseg, 0, B.cg_part.p);
+      k_bcg_partial<<<nblk, kBcgThreads, 0, bst>>>(d_items, d_segs, d_blk, 1, B.cg_part.p);
+      k_bcg_scalar<<<ceil_div(nseg, 64), 64, 0, bst>>>(d_items, d_segs, nseg, 1, B.cg_part.p);
+      k_bcg_p<<<nblk, kBcgThreads, 0, bst>>>(d_items, d_segs, d_blk);
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(bst, &g);
+    if (ce != cudaSuccess || !g) {
+      if (g) cudaGraphDestroy(g);
+      DW_CUDA(ce);
+      fail(DWFMM_ERR_CUDA, "capture of the batched CG iterations failed");
+    }
+    cudaGraphExec_t e = nullptr;
+    if (cudaGraphInstantiate(&e, g, 0) != cudaSuccess) {
+      cudaGraphDestroy(g);
+      (void)cudaGetLastError();
+      fail(DWFMM_ERR_CUDA, "instantiation of the batched CG iterations failed");
+    }
+    B.cg_graph = g;
+    B.cg_exec = e;
+    B.cg_iters = iters;
+    B.cg_nseg = nseg;
+    B.cg_nblk = nblk;
+  }
+  if (iters > 0) DW_CUDA(cudaGraphLaunch(B.cg_exec, s));
+  DW_CUDA(cudaGetLastError());
+  for (int i = 0; i < B.P; ++i) cg_snapshot(*B.plans[i], s);
 }
 
 }  // namespace dw

@@ -294,6 +294,8 @@ struct Plan {
   DBuf<float> sym_fwd;
   DBuf<unsigned long long> sym_acc;
   DBuf<unsigned> sym_colmax;
+  DBuf<uint16_t> sym_xa16, sym_xb16;   // FP16 hi/lo coordinate blocks (2x' and x') of the Gaussian path
+  bool sym_x16_ok = false;
   int near_engine = -1;   // engine of the last near field (dwfmm_near_engine)
   cudaEvent_t ev_scaled = nullptr;
   DBuf<int> d_err;   // device error flag (3 = a bounded wait timed out)
@@ -378,6 +380,19 @@ dwfmm_status direct_sum_noalloc(int kernel, double sigma, const double* pts, int
                                 cudaStream_t s);
 
 // ---- solve (solve.cu) ----
+// device state of one plan's incremental CG (layout of cg_begin)
+struct CgPtrs {
+  double *p, *ap, *c, *r;
+  double *rr, *pap, *coef, *bn2, *tmp;
+  const double* rtol2;
+  int *status, *iters;
+  int64_t n;
+  int R;
+  double lam;
+};
+CgPtrs cg_ptrs(Plan& P);
+void cg_snapshot(Plan& P, cudaStream_t s);
+void batch_cg_step(Batch& B, int iters, cudaStream_t s);
 dwfmm_status solve(Plan& P, double lambda, const double* f, double* c, int R, int64_t ld,
                    double rtol, int maxit, int* iters, double* relres);
 void cg_begin(Plan& P, double lam, const double* f, int R, int64_t ld, double rtol);

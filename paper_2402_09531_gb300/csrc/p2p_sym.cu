@@ -186,6 +186,36 @@ __device__ __forceinline__ void tmem_ld4x2(uint32_t ta, uint32_t tb, uint32_t* r
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// 16 columns, load only: the registers are valid after tmem_wait_ld16 on
+// the same array (which names them, so no use moves above the wait).
+__device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld16(uint32_t* r) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+               :
+               : "memory");
+}
+
+// 32 columns of the warp's TMEM lanes in one load, one wait.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
+      "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 struct SymArgs {
   const float* pts;          // scaled blocks [L][D+1][ld] (coordinates, row D = |x'|^2)
   int64_t gstride;           // (D+1) * ld
@@ -595,6 +625,417 @@ __global__ void k_sym_finish(const float* fwd, const unsigned long long* acc, do
   ynear[g * ystride + static_cast<int64_t>(r) * ld + s] = static_cast<float>(v);
 }
 
+// ---------------------------------------------------------------------------
+// Gaussian variant with the exponent on the tensor cores.
+//
+// For the factored Gaussian the exponent is a dot product, G = 2 x'.s'
+// (padded dimension <= 16), so it is one more small contraction:
+// G = X2 S^T with X2 = 2x' of the 256 targets (A, M = 128 per tile) and S =
+// s' of the chunk's 64 sources (B, N = 64), both as FP16 hi + lo, K = 16.
+// The two small products (hi*lo, lo*hi) are accumulated first and the large
+// one (hi*hi) last, so the accumulator's round-toward-zero step applies
+// once at the magnitude of G: ~1 ulp of |G| <= 2 * bound, as the FP32
+// multiply-add chain.  The CUDA cores only read G from tensor memory,
+// apply ex2, split E' into FP16 hi / lo and store the E tile; the rest
+// (forward and transposed products, folds, fixed-point flushes) is the
+// kernel above.
+//
+// Coordinate blocks [L][2 (hi, lo)][ld/8][2][128 B]: core (p/8, k/8) of
+// point p, coordinate k (8 FP16 per row); the target tile of T (2x') stays
+// resident, the source chunk (x') comes with the stage.
+// ---------------------------------------------------------------------------
+
+constexpr int kKD = 16;                                  // padded dimension of the G contraction
+constexpr uint32_t kIdG = idesc_f16(128, 64, 0);
+constexpr int kXBytesLeaf256 = 2 * 256 * kKD * 2;        // 16 KB
+constexpr int kXChunkHalf = (kChunk / 8) * (kKD / 8) * 128;   // 2 KB: one of hi / lo of a chunk
+
+// hi / lo FP16 coordinate blocks: xa = 2x' (target role), xb = x' (source role)
+__global__ void k_sym_make_x16(const float* pts, int64_t gstride, int L, int ld, int D, uint16_t* xa, uint16_t* xb) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= static_cast<int64_t>(L) * ld * kKD) return;
+  const int k = static_cast<int>(i % kKD);
+  const int64_t gp = i / kKD;
+  const int p = static_cast<int>(gp % ld);
+  const int64_t g = gp / ld;
+  const float v = k < D ? pts[g * gstride + static_cast<int64_t>(k) * ld + p] : 0.0f;
+  const float h = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
+  const __half hh = __float2half_rn(h), hl = __float2half_rn(v - h);
+  const __half ah = __float2half_rn(2.0f * h), al = __float2half_rn(2.0f * (v - h));
+  const int64_t blk = g * static_cast<int64_t>(ld) * kKD * 2;            // halfs per leaf
+  const int64_t off = (p / 8) * (kKD / 8) * 64 + (k / 8) * 64 + (p % 8) * 8 + (k % 8);
+  const int64_t lo = static_cast<int64_t>(ld) * kKD;                      // hi -> lo
+  xb[blk + off] = __half_as_ushort(hh);
+  xb[blk + lo + off] = __half_as_ushort(hl);
+  xa[blk + off] = __half_as_ushort(ah);
+  xa[blk + lo + off] = __half_as_ushort(al);
+}
+
+struct SymGArgs {
+  const uint16_t* xa;        // [L][2][ld/8][2][64] 2x' hi / lo
+  const uint16_t* xb;        // x' hi / lo
+  const uint16_t* bq;        // FP16 charge blocks [L][ld/8][4][64]
+  const int32_t* uprow;
+  const int32_t* ups;
+  const int32_t* order;
+  float* fwd;
+  unsigned long long* acc;
+  float acc_scale;
+  int ld;                    // 256
+  int* err;
+};
+
+__global__ void __launch_bounds__(kSymThreads, 1) k_near_sym_gtc(SymGArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bars[32];
+  __shared__ uint32_t tmem_slot;
+  uint64_t* full = bars;            // [3] TMA landed (coordinates + charges of a chunk)
+  uint64_t* sfree = bars + 3;       // [3] stage read by the MMAs
+  uint64_t* efull = bars + 6;       // [2] E tile written (16 warps)
+  uint64_t* efree = bars + 8;       // [2] E tile read by the MMAs
+  uint64_t* tfull = bars + 10;      // [2] transposed accumulator complete
+  uint64_t* tempty = bars + 12;     // [2] transposed accumulator drained (16 warps)
+  uint64_t* cready = bars + 14;     // [2] lo rows combined (8 warps)
+  uint64_t* ffull = bars + 16;      // [2] forward accumulators of an entry complete
+  uint64_t* fempty = bars + 18;     // [2] forward accumulators folded (16 warps)
+  uint64_t* gfull = bars + 20;      // [2] G of a chunk complete
+  uint64_t* gfree = bars + 22;      // [2] G read by the compute warps (16 warps)
+  uint64_t* qfull = bars + 24;      // q_T and 2x'_T landed
+  uint64_t* fin = bars + 25;
+
+  const int ld = a.ld;              // 256: two 128-target tiles, four 64-source chunks
+  constexpr int NT = 2, NC = 4;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int T = a.order[blockIdx.x];
+  const int e0 = a.uprow[T], ne = a.uprow[T + 1] - e0;
+  const int nchunks = ne * NC;
+
+  constexpr uint32_t ebytes = NT * 16 * kTS;                         // 64 KB
+  constexpr uint32_t stage_bytes = 2 * kXChunkHalf + kQChunkBytes;  // 8 KB
+  unsigned char* ebuf = smem;
+  unsigned char* stages = smem + 2 * ebytes;
+  unsigned char* qT = stages + kStages * stage_bytes;               // 16 KB
+  unsigned char* xT = qT + ld * 64;                                  // 16 KB
+  float* comb = reinterpret_cast<float*>(xT + kXBytesLeaf256);      // [2][16][64]
+  constexpr uint32_t kG = 0, kF = 256, kTr = 384;                    // TMEM column bases
+
+  if (t == 0) {
+    for (int i = 0; i < kStages; ++i) {
+      bar_init(&full[i], 1);
+      bar_init(&sfree[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      bar_init(&efull[i], kSymCompWarps);
+      bar_init(&efree[i], 1);
+      bar_init(&tfull[i], 1);
+      bar_init(&tempty[i], kSymCompWarps);
+      bar_init(&cready[i], kSymCompWarps / 2);
+      bar_init(&ffull[i], 1);
+      bar_init(&fempty[i], kSymCompWarps);
+      bar_init(&gfull[i], 1);
+      bar_init(&gfree[i], kSymCompWarps);
+    }
+    bar_init(qfull, 1);
+    bar_init(fin, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tmem_alloc(&tmem_slot, 512);
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = tmem_slot;
+
+  if (warp == kSymCompWarps + 1) {
+    // ---- TMA producer
+    if (lane == 0) {
+      bool bad = false;
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      bar_expect_tx(qfull, static_cast<uint32_t>(ld * 64 + kXBytesLeaf256));
+      bulk_load(qT, a.bq + static_cast<int64_t>(T) * ld * 32, static_cast<uint32_t>(ld * 64), qfull);
+      bulk_load(xT, a.xa + static_cast<int64_t>(T) * ld * kKD * 2, kXBytesLeaf256, qfull);
+      int i = 0;
+      for (int e = 0; e < ne && !bad; ++e) {
+        const int S = a.ups[e0 + e];
+        const uint16_t* xs = a.xb + static_cast<int64_t>(S) * ld * kKD * 2;
+        for (int c = 0; c < NC; ++c, ++i) {
+          const int st = i % kStages;
+          if (i >= kStages && !wait_sleep(&sfree[st], static_cast<uint32_t>(((i - kStages) / kStages) & 1))) {
+            bad = true;
+            break;
+          }
+          unsigned char* dst = stages + st * stage_bytes;
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          bar_expect_tx(&full[st], stage_bytes);
+          bulk_load(dst, xs + c * (kXChunkHalf / 2), kXChunkHalf, &full[st]);
+          bulk_load(dst + kXChunkHalf, xs + static_cast<int64_t>(ld) * kKD + c * (kXChunkHalf / 2), kXChunkHalf,
+                    &full[st]);
+          bulk_load(dst + 2 * kXChunkHalf, a.bq + (static_cast<int64_t>(S) * ld + c * kChunk) * 32, kQChunkBytes,
+                    &full[st]);
+        }
+      }
+      (void)wait_sleep(qfull, 0u);
+      for (int j = i > kStages ? i - kStages : 0; j < i; ++j)
+        (void)wait_sleep(&full[j % kStages], static_cast<uint32_t>((j / kStages) & 1));
+      if (bad) atomicExch(a.err, 3);
+    }
+  } else if (warp == kSymCompWarps) {
+    // ---- MMA issuer: G of chunk i + 1 ahead of the products of chunk i
+    if (lane == 0) {
+      bool bad = !wait_sleep(qfull, 0u);
+      const uint32_t ebase = sptr(ebuf), sbase = sptr(stages), qtb = sptr(qT), xtb = sptr(xT);
+      constexpr uint32_t xlo = 256 * kKD * 2;            // hi -> lo in the target block (bytes)
+      // G MMAs of chunk i (stage i % kStages) into G buffer i & 1
+      // descriptors: the start address is the low field (address / 16), so a
+      // byte offset o moves a descriptor by o / 16
+      const u64 dG_b = smem_desc(sbase, 128, 256);                  // stage 0 coordinates (hi)
+      const u64 dG_a = smem_desc(xtb, 128, 256);                    // target tile 0 (hi)
+      const u64 dF_a = smem_desc(ebase, 128, kTS);                  // E tile 0, forward A (hi)
+      const u64 dF_b = smem_desc(sbase + 2 * kXChunkHalf, 512, 128);   // stage 0 charges
+      const u64 dT_a = smem_desc(ebase, kSymTrnLbo, kSymTrnSbo);    // E tile 0, transposed A
+      const u64 dT_b = smem_desc(qtb, 512, 128);                     // q_T
+      auto issue_g = [&](int i) -> bool {
+        const int st = i % kStages, gb = i & 1;
+        if (!wait_sleep(&full[st], static_cast<uint32_t>((i / kStages) & 1))) return false;
+        if (i >= 2 && !wait_sleep(&gfree[gb], static_cast<uint32_t>(((i - 2) >> 1) & 1))) return false;
+        fence_after();
+        const u64 bhi = dG_b + ((st * stage_bytes) >> 4), blo = bhi + (kXChunkHalf >> 4);
+#pragma unroll
+        for (int at = 0; at < NT; ++at) {
+          const u64 ahi = dG_a + ((at * 16 * 256) >> 4), alo = ahi + (xlo >> 4);
+          const uint32_t d = tmem + kG + static_cast<uint32_t>(gb * 128 + at * 64);
+          mma_f16(d, ahi, blo, kIdG, 0u);                // small terms first,
+          mma_f16(d, alo, bhi, kIdG, 1u);
+          mma_f16(d, ahi, bhi, kIdG, 1u);                // the large one last
+        }
+        mma_commit(&gfull[gb]);
+        return true;
+      };
+      int jt = 0;
+      if (nchunks > 0 && !bad) bad = !issue_g(0);
+      int i = 0;
+      for (int e = 0; e < ne && !bad; ++e) {
+        const int S = a.ups[e0 + e];
+        const bool diag = S == T;
+        const int fb = e & 1;
+        for (int c = 0; c < NC; ++c, ++i) {
+          if (i + 1 < nchunks && !issue_g(i + 1)) {
+            bad = true;
+            break;
+          }
+          const int st = i % kStages, eb = i & 1;
+          if (!wait_sleep(&efull[eb], static_cast<uint32_t>((i >> 1) & 1)) ||
+              (c == 0 && e >= 2 && !wait_sleep(&fempty[fb], static_cast<uint32_t>(((e - 2) >> 1) & 1)))) {
+            bad = true;
+            break;
+          }
+          fence_after();
+          const u64 fa = dF_a + ((eb * ebytes) >> 4);
+          const u64 fb_desc = dF_b + ((st * stage_bytes) >> 4);
+#pragma unroll
+          for (int at = 0; at < NT; ++at) {
+            const uint32_t dcol = tmem + kF + static_cast<uint32_t>(fb * 64 + at * 32);
+#pragma unroll
+            for (int kk = 0; kk < kChunk / 16; ++kk) {
+              const u64 ahi = fa + ((at * 16 * kTS + kk * 2 * 128) >> 4);
+              const u64 bq = fb_desc + ((kk * 2 * 512) >> 4);
+              mma_f16(dcol, ahi, bq, kIdFwd32, (c > 0 || kk > 0) ? 1u : 0u);
+              mma_f16(dcol + 16, ahi + (kHL >> 4), bq, kIdFwd16, 1u);
+            }
+          }
+          if (!diag) {
+            const int tb = jt & 1;
+            if (jt >= 2 && !wait_sleep(&tempty[tb], static_cast<uint32_t>(((jt - 2) >> 1) & 1))) {
+              bad = true;
+              break;
+            }
+            fence_after();
+            const uint32_t dcol = tmem + kTr + static_cast<uint32_t>(tb * 32);
+            const u64 ta = dT_a + ((eb * ebytes) >> 4);
+#pragma unroll
+            for (int j = 0; j < NT * 8; ++j)
+              mma_f16(dcol, ta + ((j * 2 * kTS) >> 4), dT_b + ((j * 2 * 512) >> 4), kIdTrn32, j > 0 ? 1u : 0u);
+            mma_commit(&tfull[tb]);
+            ++jt;
+          }
+          mma_commit(&efree[eb]);
+          mma_commit(&sfree[st]);
+          if (c == NC - 1) mma_commit(&ffull[fb]);
+        }
+      }
+      mma_commit(fin);
+      (void)wait_sleep(fin, 0u);
+      if (bad) atomicExch(a.err, 3);
+    }
+  } else {
+    // ---- compute warps: (quadrant qd, part p): target tile p / 2, sources 32 (p % 2) .. + 31 of each chunk
+    const int qd = warp & 3, part = warp >> 2;
+    const int at = part >> 1, sh = part & 1;
+    const int tl = qd * 32 + lane;                 // target within the tile (TMEM lane)
+    const int tt = at * 128 + tl;                  // target within T
+    const uint32_t lane_base = tmem + (static_cast<uint32_t>(qd * 32) << 16);
+    // Kahan sums in registers: tile `at`, right-hand sides 8 sh .. 8 sh + 7
+    float ks[8], kc[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) ks[r] = kc[r] = 0.0f;
+    bool bad = false;
+
+    auto fold = [&](int e) {
+      const int fb = e & 1;
+      const bool ok = wait_sleep(&ffull[fb], static_cast<uint32_t>((e >> 1) & 1));
+      if (__any_sync(0xffffffffu, !ok)) {
+        bad = true;
+        return;
+      }
+      fence_after();
+      uint32_t dv[8], dl[8];
+      const uint32_t col = lane_base + kF + static_cast<uint32_t>(fb * 64 + at * 32 + 8 * sh);
+      tmem_ld8x2(col, col + 16, dv, dl);
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const float y = (__uint_as_float(dv[r]) + __uint_as_float(dl[r])) - kc[r];
+        const float s = ks[r] + y;
+        kc[r] = (s - ks[r]) - y;
+        ks[r] = s;
+      }
+      fence_before();
+      __syncwarp();
+      if (lane == 0) bar_arrive(&fempty[fb]);
+    };
+    auto flush = [&](int jt, int S, int c) {
+      const int tb = jt & 1;
+      const bool ok = wait_sleep(&tfull[tb], static_cast<uint32_t>((jt >> 1) & 1));
+      if (__any_sync(0xffffffffu, !ok)) {
+        bad = true;
+        return;
+      }
+      fence_after();
+      const int r0 = 4 * part;
+      const uint32_t col = lane_base + kTr + static_cast<uint32_t>(tb * 32 + r0);
+      uint32_t x[4], y[4];
+      tmem_ld4x2(col, col + 16, x, y);
+      float* cb = comb + tb * (64 * 16);
+      if (qd >= 2) {
+        const int s = (qd - 2) * 32 + lane;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) cb[(r0 + j) * 64 + s] = __uint_as_float(x[j]) + __uint_as_float(y[j]);
+        fence_before();
+        __syncwarp();
+        if (lane == 0) {
+          bar_arrive(&cready[tb]);
+          bar_arrive(&tempty[tb]);
+        }
+      } else {
+        const int s = qd * 32 + lane;
+        const bool okc = wait_sleep(&cready[tb], static_cast<uint32_t>((jt >> 1) & 1));
+        if (__any_sync(0xffffffffu, !okc)) {
+          bad = true;
+          fence_before();
+          if (lane == 0) bar_arrive(&tempty[tb]);
+          return;
+        }
+        unsigned long long* dst = a.acc + (static_cast<int64_t>(S) * 16 + r0) * ld + c * kChunk + s;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float v = (__uint_as_float(x[j]) + __uint_as_float(y[j])) + cb[(r0 + j) * 64 + s];
+          red_add_u64(dst + static_cast<int64_t>(j) * ld, __float2ll_rn(v * a.acc_scale));
+        }
+        fence_before();
+        __syncwarp();
+        if (lane == 0) bar_arrive(&tempty[tb]);
+      }
+    };
+
+    int i = 0, jt = 0;
+    int pend_jt = -1, pend_S = 0, pend_c = 0;
+    for (int e = 0; e < ne && !bad; ++e) {
+      const int S = a.ups[e0 + e];
+      const bool diag = S == T;
+      for (int c = 0; c < NC; ++c, ++i) {
+        const int gb = i & 1, eb = i & 1;
+        // G[t][32 sources] from tensor memory, then the G buffer is free
+        const bool okg = wait_sleep(&gfull[gb], static_cast<uint32_t>((i >> 1) & 1));
+        if (__any_sync(0xffffffffu, !okg)) {
+          bad = true;
+          break;
+        }
+        fence_after();
+        // G in two halves: the second half's load is in flight while the
+        // first half is evaluated
+        uint32_t g[32];
+        const uint32_t gaddr = lane_base + kG + static_cast<uint32_t>(gb * 128 + at * 64 + 32 * sh);
+        tmem_ld16(gaddr, g);
+        tmem_ld16_async(gaddr + 16, g + 16);
+        const bool oke = i < 2 || wait_sleep(&efree[eb], static_cast<uint32_t>(((i - 2) >> 1) & 1));
+        const uint32_t et = sptr(ebuf + eb * ebytes) +
+                            static_cast<uint32_t>((tt >> 3) * kTS + (tt & 7) * 16 + (4 * sh) * 128);
+        if (__all_sync(0xffffffffu, oke)) {
+#pragma unroll
+          for (int q8 = 0; q8 < 2; ++q8) {
+            uint32_t hi[4], lo[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              split_f16x2(ex2f(__uint_as_float(g[8 * q8 + 2 * u])), ex2f(__uint_as_float(g[8 * q8 + 2 * u + 1])),
+                          hi[u], lo[u]);
+            sts128(et + q8 * 128, hi);
+            sts128(et + q8 * 128 + kHL, lo);
+          }
+        }
+        tmem_wait_ld16(g + 16);
+        fence_before();
+        __syncwarp();
+        if (lane == 0) bar_arrive(&gfree[gb]);
+        if (__any_sync(0xffffffffu, !oke)) {
+          bad = true;
+          break;
+        }
+#pragma unroll
+        for (int q8 = 2; q8 < 4; ++q8) {
+          uint32_t hi[4], lo[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            split_f16x2(ex2f(__uint_as_float(g[8 * q8 + 2 * u])), ex2f(__uint_as_float(g[8 * q8 + 2 * u + 1])), hi[u],
+                        lo[u]);
+          sts128(et + q8 * 128, hi);
+          sts128(et + q8 * 128 + kHL, lo);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) bar_arrive(&efull[eb]);
+        if (pend_jt >= 0) {
+          flush(pend_jt, pend_S, pend_c);
+          pend_jt = -1;
+          if (bad) break;
+        }
+        if (c == 0 && e >= 1) {
+          fold(e - 1);
+          if (bad) break;
+        }
+        if (!diag) {
+          pend_jt = jt;
+          pend_S = S;
+          pend_c = c;
+          ++jt;
+        }
+      }
+    }
+    if (!bad && pend_jt >= 0) flush(pend_jt, pend_S, pend_c);
+    if (!bad && ne >= 1) fold(ne - 1);
+    if (bad && lane == 0) atomicExch(a.err, 3);
+    float* op = a.fwd + static_cast<int64_t>(T) * 16 * ld + tt;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) op[(8 * sh + r) * ld] = ks[r];
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 0) tmem_dealloc(tmem, 512);
+}
+
+size_t sym_g_smem() {
+  return 2 * static_cast<size_t>(2 * 16 * kTS) + kStages * static_cast<size_t>(2 * kXChunkHalf + kQChunkBytes) +
+         256 * 64 + kXBytesLeaf256 + 2 * 64 * 16 * 4;
+}
+
 size_t sym_smem(int D, int ld) {
   const int NT = ld / 128;
   const size_t ebytes = static_cast<size_t>(NT) * 16 * kTS;
@@ -621,6 +1062,12 @@ void sym_attrs_d(int bytes) {
 
 std::atomic<uint64_t> g_sym_attrs_dev{0};
 constexpr int kSymSmemMax = 220 * 1024;
+
+// The exponent on the tensor cores: Gaussian in factored form, leaves of 256
+// slots, padded dimension <= 16.
+bool sym_g_applies(const Plan& P, int D) {
+  return P.kernel == DWFMM_K_GAUSS && P.m_pad == 256 && D <= kKD && sym_g_smem() <= static_cast<size_t>(kSymSmemMax);
+}
 
 }  // namespace
 
@@ -667,6 +1114,7 @@ bool near_sym_tc(Plan& P, int D, int Rc, cudaStream_t s) {
     sym_attrs_d<12>(kSymSmemMax);
     sym_attrs_d<16>(kSymSmemMax);
     sym_attrs_d<20>(kSymSmemMax);
+    cudaFuncSetAttribute(k_near_sym_gtc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSymSmemMax);
     DW_CUDA(cudaGetLastError());
     g_sym_attrs_dev.fetch_or(dbit);
   }
@@ -685,6 +1133,35 @@ bool near_sym_tc(Plan& P, int D, int Rc, cudaStream_t s) {
   k_sym_make_bq<<<ceil_div(static_cast<int64_t>(P.L) * ld * 16, 256), 256, 0, s>>>(
       P.xb32.p, P.d_ptsk.p, gstride, P.L, ld, D, gauss, Rc, P.sym_colmax.p, P.sym_bq16.p);
   const int sb = sym_tc_bits(P);
+  if (sym_g_applies(P, D)) {
+    P.near_engine = 5;
+    if (!P.sym_x16_ok) {
+      P.sym_xa16.alloc(static_cast<size_t>(P.L) * ld * kKD * 2);
+      P.sym_xb16.alloc(static_cast<size_t>(P.L) * ld * kKD * 2);
+      k_sym_make_x16<<<ceil_div(static_cast<int64_t>(P.L) * ld * kKD, 256), 256, 0, s>>>(
+          P.d_ptsk.p, gstride, P.L, ld, D, P.sym_xa16.p, P.sym_xb16.p);
+      P.sym_x16_ok = true;
+    }
+    SymGArgs g{};
+    g.xa = P.sym_xa16.p;
+    g.xb = P.sym_xb16.p;
+    g.bq = P.sym_bq16.p;
+    g.uprow = P.sym_uprow.p;
+    g.ups = P.sym_s.p;
+    g.order = P.sym_order.p;
+    g.fwd = P.sym_fwd.p;
+    g.acc = P.sym_acc.p;
+    g.acc_scale = std::ldexp(1.0f, sb);
+    g.ld = ld;
+    g.err = P.d_err.p;
+    k_near_sym_gtc<<<P.L, kSymThreads, sym_g_smem(), s>>>(g);
+    DW_CUDA(cudaGetLastError());
+    k_sym_finish<<<ceil_div(nsite, 256), 256, 0, s>>>(P.sym_fwd.p, P.sym_acc.p, std::ldexp(1.0, -sb), P.d_ptsk.p,
+                                                       gstride, P.L, ld, D, gauss, Rc, P.sym_colmax.p, P.ynear32.p,
+                                                       static_cast<int64_t>(kRC) * ld);
+    DW_CUDA(cudaGetLastError());
+    return true;
+  }
   SymArgs a{};
   a.pts = P.d_ptsk.p;
   a.gstride = gstride;

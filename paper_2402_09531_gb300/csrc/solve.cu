@@ -9,6 +9,7 @@
 // float64 operator, the inner CG the plan's reduced-precision operator.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "dwfmm_internal.cuh"
@@ -313,6 +314,43 @@ void refine_step(Plan& P, double lam, double* c, const double* delta, double* r,
   k_axpby<<<ceil_div(nr, 256), 256, 0, P.stream>>>(delta, c, nullptr, dev3 + 2 * R, 1.0, nullptr, 0.0, n, n, R, 1.0);
   k_axpby<<<ceil_div(nr, 256), 256, 0, P.stream>>>(w, r, nullptr, dev3 + 2 * R, 1.0, nullptr, 0.0, n, n, R, -1.0);
   DW_CUDA(cudaGetLastError());
+}
+
+// Device pointers of a plan's incremental CG state (for the batched step).
+CgPtrs cg_ptrs(Plan& P) {
+  CgState& S = P.cgs;
+  const int R = S.R;
+  double* part = P.cg_dot.p;
+  CgPtrs c;
+  std::memset(&c, 0, sizeof(c));   // padding too: batches compare the bytes
+  c.p = P.cg_p.p;
+  c.ap = P.cg_ap.p;
+  c.c = P.cg_c.p;
+  c.r = P.cg_r.p;
+  c.rr = part + kDotBlocks * R;
+  c.pap = c.rr + R;
+  c.coef = c.pap + R;
+  c.bn2 = c.coef + R;
+  c.tmp = c.bn2 + R;
+  c.rtol2 = c.tmp + R;
+  c.status = S.d_int.p;
+  c.iters = S.d_int.p + R;
+  c.n = P.N;
+  c.R = R;
+  c.lam = S.lam;
+  return c;
+}
+
+// Status snapshot of the plan's CG for dwfmm_cg_poll, on stream s.
+void cg_snapshot(Plan& P, cudaStream_t s) {
+  CgState& S = P.cgs;
+  const int R = S.R;
+  double* rr = P.cg_dot.p + kDotBlocks * R;
+  DW_CUDA(cudaMemcpyAsync(S.h_snap, S.d_int.p, 2 * R * sizeof(int), cudaMemcpyDeviceToHost, s));
+  DW_CUDA(cudaMemcpyAsync(reinterpret_cast<char*>(S.h_snap) + 128 * sizeof(int), rr, R * sizeof(double),
+                          cudaMemcpyDeviceToHost, s));
+  DW_CUDA(cudaEventRecord(S.ev, s));
+  S.stepped = true;
 }
 
 void cg_begin(Plan& P, double lam, const double* f, int R, int64_t ld, double rtol) {

@@ -36,7 +36,8 @@ EXPORTS = ("dwfmm_plan_create", "dwfmm_plan_set_nodes", "dwfmm_tree_build", "dwf
            "dwfmm_set_profiling", "dwfmm_phase_times", "dwfmm_direct_sum_noalloc",
            "dwfmm_cg_begin", "dwfmm_cg_step", "dwfmm_cg_poll", "dwfmm_cg_result", "dwfmm_residual",
            "dwfmm_refine",
-           "dwfmm_batch_create", "dwfmm_batch_matvec", "dwfmm_batch_info", "dwfmm_batch_destroy",
+           "dwfmm_batch_create", "dwfmm_batch_matvec", "dwfmm_batch_info", "dwfmm_batch_cg_step",
+           "dwfmm_batch_destroy",
            "dwfmm_evaluate")
 
 
@@ -87,6 +88,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "dwfmm_batch_create": (i32, [P, P, i32, P, C.POINTER(P)]),
         "dwfmm_batch_matvec": (i32, [P, P, P, P]),
         "dwfmm_batch_info": (i32, [P, C.POINTER(i32), P, C.POINTER(i64)]),
+        "dwfmm_batch_cg_step": (i32, [P, i32, P]),
         "dwfmm_batch_destroy": (i32, [P]),
         "dwfmm_evaluate": (i32, [P, P, i64, i64, P, i64, P, i64, i32, P]),
     }
@@ -332,7 +334,8 @@ class Plan:
         return int(nx.value), int(nf.value), int(nn.value), int(dep.value)
 
     NEAR_ENGINES = {-1: "none", 0: "fp64_list", 1: "fp64_symmetric", 2: "fp32_cuda_cores",
-                    3: "mixed_tf32_tensor", 4: "mixed_symmetric_fp16_tensor"}
+                    3: "mixed_tf32_tensor", 4: "mixed_symmetric_fp16_tensor",
+                    5: "mixed_symmetric_fp16_tensor_exponent"}
 
     def near_engine(self) -> str:
         """Engine that evaluated the near field in the last matvec."""
@@ -410,6 +413,14 @@ class Batch:
         st = self._l.dwfmm_batch_matvec(self.h, xp, yp, _stream_handle(stream))
         if st != OK:
             raise DwfmmError(st, self._l.dwfmm_status_string(st).decode())
+
+    def cg_step(self, iters: int, stream=None):
+        """`iters` CG iterations of every problem (each begun with
+        Plan.cg_begin); one fused batch matvec per iteration."""
+        st = self._l.dwfmm_batch_cg_step(self.h, int(iters), _stream_handle(stream))
+        if st != OK:
+            msg = self._l.dwfmm_last_error(self.plans[0].h).decode() if self.plans else ""
+            raise DwfmmError(st, msg or self._l.dwfmm_status_string(st).decode())
 
     def info(self):
         split = C.c_int32(0)

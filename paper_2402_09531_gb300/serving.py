@@ -13,6 +13,15 @@ operator (dwfmm_refine), and float32/mixed plans restart the inner CG on
 the float64 residual until it meets the request's tolerance.  Finished requests
 release their slot, memory and plan.
 
+With batched=True (float32 / mixed plans) the active requests that share a
+configuration (kernel, dimension, weights, index set, leaf size, right-hand
+sides) also share one CUDA stream and one batch: every pass advances all of
+them with dwfmm_batch_cg_step, whose matvec is one fused launch sequence
+over all their problems (their near fields in one launch, their couplings in
+another).  The batch is rebuilt whenever a request joins or leaves the group;
+each request's Krylov state stays in its own plan, so a rebuild moves
+nothing.
+
 This module only schedules; every numerical step runs in libdwfmm.so.
 """
 from __future__ import annotations
@@ -23,7 +32,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from .dwfmm import Plan
+from .dwfmm import Batch, Plan
 
 
 @dataclass
@@ -92,14 +101,29 @@ class _Active:
     refinements: int = 0
 
 
+@dataclass
+class _Group:
+    """Requests with one configuration, advanced together (batched mode)."""
+    stream: object
+    members: list = field(default_factory=list)
+    batch: object = None
+    dirty: bool = True
+    event: object = None      # recorded after the last batched step
+
+
 class Server:
     """Admission by memory and slots; all active solves advance concurrently."""
 
     def __init__(self, precision: str = "fp32", max_active: int = 8, mem_budget: int | None = None,
                  step_iters: int = 8, device: int = 0, inner_rtol: float | None = None,
-                 inner_maxit: int | None = None):
+                 inner_maxit: int | None = None, batched: bool = False):
         import torch
         self.torch = torch
+        if batched and precision == "fp64":
+            raise ValueError("batched serving runs float32 / mixed plans (batches are float32)")
+        self.batched = batched
+        self.groups: dict = {}        # configuration key -> _Group (batched mode)
+        self.batch_rebuilds = 0
         self.dev = torch.device("cuda", device)
         self.precision = precision
         self.max_active = max_active
@@ -140,7 +164,13 @@ class Server:
     # -- request lifecycle ------------------------------------------------------
     def _admit(self, r: Request, t_now: float) -> _Active:
         torch = self.torch
-        stream = torch.cuda.Stream(self.dev)
+        if self.batched:
+            g = self.groups.get(self._key(r))
+            if g is None:
+                g = self.groups[self._key(r)] = _Group(torch.cuda.Stream(self.dev))
+            stream = g.stream
+        else:
+            stream = torch.cuda.Stream(self.dev)
         key, plan = self._take_plan(r, stream)
         nbytes = estimate_bytes(r.X.shape[0], r.X.shape[1], r.f.shape[0], r.leaf, plan.n_x)
         with torch.cuda.stream(stream):
@@ -150,9 +180,15 @@ class Server:
             res = f0.clone()   # the residual of acc = 0
         plan.tree_build(Xd, stream=stream)
         plan.cg_begin(r.lam, f0, rtol=self._inner_tol(r.rtol, 1.0), stream=stream)
-        plan.cg_step(self.step_iters, stream=stream)
+        if not self.batched:
+            plan.cg_step(self.step_iters, stream=stream)
         self.used += nbytes
-        return _Active(r, plan, stream, key, f0, f0, acc, res, t_now, nbytes)
+        a = _Active(r, plan, stream, key, f0, f0, acc, res, t_now, nbytes)
+        if self.batched:
+            g = self.groups[key]
+            g.members.append(a)
+            g.dirty = True
+        return a
 
     def _finish(self, a: _Active, status: str, relres, t_now: float) -> Result:
         torch = self.torch
@@ -182,7 +218,8 @@ class Server:
         total = a.iters + a_iters
         inner_cap = self.inner_maxit if self.inner_maxit is not None else a.req.maxit
         if running and total < a.req.maxit and a_iters < inner_cap:
-            a.plan.cg_step(self.step_iters, stream=a.stream)
+            if not self.batched:
+                a.plan.cg_step(self.step_iters, stream=a.stream)
             return None
         # inner solve finished: fold its correction in (dwfmm_refine: the plain
         # step where it lowers the float64 residual, else the minimal-residual
@@ -202,7 +239,8 @@ class Server:
         a.refinements += 1
         a.fd = a.r
         a.plan.cg_begin(a.req.lam, a.r, rtol=self._inner_tol(a.req.rtol, float(np.max(rel))), stream=a.stream)
-        a.plan.cg_step(self.step_iters, stream=a.stream)
+        if not self.batched:
+            a.plan.cg_step(self.step_iters, stream=a.stream)
         return None
 
     def run(self, requests: list) -> list:
@@ -228,17 +266,60 @@ class Server:
                 active.append(self._admit(r, now))
             self.peak_active = max(self.peak_active, len(active))
             progressed = False
-            for a in list(active):
-                res = self._advance(a, time.perf_counter() - t0)
-                if res is not None:
-                    active.remove(a)
-                    done.append(res)
-                    progressed = True
+            if self.batched:
+                progressed = self._step_groups(active, done, t0)
+            else:
+                for a in list(active):
+                    res = self._advance(a, time.perf_counter() - t0)
+                    if res is not None:
+                        active.remove(a)
+                        done.append(res)
+                        progressed = True
             if not progressed and not queue:
                 time.sleep(20e-6)
         return done
 
+    def _step_groups(self, active: list, done: list, t0: float) -> bool:
+        """Batched mode: for every group whose last step has finished, handle
+        its members' finished inner solves, rebuild the batch if the
+        membership changed, and enqueue the next batched step."""
+        torch = self.torch
+        progressed = False
+        for key, g in list(self.groups.items()):
+            if g.event is not None and not g.event.query():
+                continue
+            for a in list(g.members):
+                if g.event is None:
+                    break                       # never stepped: nothing to poll yet
+                res = self._advance(a, time.perf_counter() - t0)
+                if res is not None:
+                    g.members.remove(a)
+                    active.remove(a)
+                    done.append(res)
+                    g.dirty = True
+                    progressed = True
+            if not g.members:
+                if g.batch is not None:
+                    g.batch.close()
+                del self.groups[key]
+                continue
+            if g.dirty:
+                if g.batch is not None:
+                    g.batch.close()
+                g.batch = Batch([a.plan for a in g.members], [a.req.f.shape[0] for a in g.members],
+                                stream=g.stream)
+                g.dirty = False
+                self.batch_rebuilds += 1
+            g.batch.cg_step(self.step_iters, stream=g.stream)
+            g.event = torch.cuda.Event()
+            g.event.record(g.stream)
+        return progressed
+
     def close(self):
+        for g in self.groups.values():
+            if g.batch is not None:
+                g.batch.close()
+        self.groups.clear()
         for plans in self.pool.values():
             for p in plans:
                 p.close()

@@ -197,3 +197,93 @@ def test_refine_step_never_raises_the_float64_residual(precision):
     assert np.all(rel2 <= 1e-9)
     p.close()
     p64.close()
+
+
+def _mixed_plans(reqs):
+    import torch
+    from paper_2402_09531_gb300 import Plan
+    plans, fs = [], []
+    for r in reqs:
+        p = Plan(d=16, kernel="exp", gamma=r.gamma, weight_rule="paper_logrho", q=6.0, eta=2.0, leaf_size=128,
+                 precision="mixed", max_rhs=1)
+        p.tree_build(torch.from_numpy(r.X).cuda())
+        plans.append(p)
+        fs.append(torch.from_numpy(r.f).cuda())
+    return plans, fs
+
+
+def test_batched_cg_matches_each_plans_own_cg():
+    """dwfmm_batch_cg_step advances the CG of four problems together (one
+    fused batch matvec per iteration, fused vector updates): every column
+    converges, in about the iterations of the plan's own CG, to the same
+    solution within the CG tolerance."""
+    import torch
+    from paper_2402_09531_gb300 import Batch
+    reqs = _requests([1400, 2100, 1000, 2600], seed0=80)
+    plans, fs = _mixed_plans(reqs)
+    lam, rtol = 1e-1, 1e-6
+    single, its1 = [], []
+    for p, f in zip(plans, fs):
+        p.cg_begin(lam, f, rtol=rtol)
+        for _ in range(400):
+            p.cg_step(16)
+            torch.cuda.synchronize()
+            ready, st, it, rr = p.cg_poll()
+            if ready and st[0] != 0:
+                break
+        assert st[0] == 1
+        its1.append(int(it[0]))
+        c = torch.empty_like(f)
+        p.cg_result(c)
+        torch.cuda.synchronize()
+        single.append(c.cpu().numpy())
+    b = Batch(plans, [1] * len(plans))
+    for p, f in zip(plans, fs):
+        p.cg_begin(lam, f, rtol=rtol)
+    for _ in range(400):
+        b.cg_step(16)
+        torch.cuda.synchronize()
+        polls = [p.cg_poll() for p in plans]
+        if all(pl[0] and pl[1][0] != 0 for pl in polls):
+            break
+    for p, f, c1, it1 in zip(plans, fs, single, its1):
+        ready, st, it, rr = p.cg_poll()
+        assert ready and st[0] == 1
+        assert abs(int(it[0]) - it1) <= max(3, it1 // 10)
+        c = torch.empty_like(f)
+        p.cg_result(c)
+        torch.cuda.synchronize()
+        c = c.cpu().numpy()
+        assert np.linalg.norm(c - c1) / np.linalg.norm(c1) <= 1e-3
+    b.close()
+    for p in plans:
+        p.close()
+
+
+def test_batched_server_same_within_tolerance_alone_and_in_the_mix():
+    """Batched serving (requests of one configuration advance together
+    through one batch): every served solve meets rtol with the oracle's
+    operator, alone and in the mix, so the two results agree in the
+    operator's norm to 2 rtol ||f||."""
+    from paper_2402_09531_gb300.serving import Request, Server
+    base = _requests([1500, 2600, 900, 3200, 2000, 1200], seed0=90)
+    reqs = [Request(rid=r.rid, X=r.X, f=r.f, kernel=r.kernel, gamma=r.gamma, q=r.q, eta=r.eta, leaf=r.leaf,
+                    weight_rule=r.weight_rule, lam=1e-2, rtol=1e-6, maxit=4000) for r in base]
+    alone = Server(precision="mixed", max_active=1, batched=True)
+    r_alone = {r.rid: alone.run([r])[0] for r in reqs[:2]}
+    alone.close()
+    mix = Server(precision="mixed", max_active=6, batched=True)
+    res = {r.rid: r for r in mix.run(reqs)}
+    assert mix.peak_active >= 4 and mix.batch_rebuilds >= 2
+    mix.close()
+    for r in reqs:
+        assert res[r.rid].status == "ok", (r.rid, res[r.rid].status)
+        assert max(res[r.rid].relres) <= r.rtol
+    for rid in (0, 1):
+        r = reqs[rid]
+        pb = o.make_problem(r.X, "exp", o.weights_paper_normalised(2 * r.gamma, 2.0), 6.0, 128, 2.0)
+        A = lambda c: o.fmm_matvec(pb, c[None])[0] + r.lam * c
+        fn = np.linalg.norm(r.f[0])
+        for c in (res[rid].c[0], r_alone[rid].c[0]):
+            assert np.linalg.norm(r.f[0] - A(c)) / fn <= 2e-6
+        assert np.linalg.norm(A(res[rid].c[0] - r_alone[rid].c[0])) / fn <= 4e-6
