@@ -187,7 +187,8 @@ dwfmm_status dwfmm_solve(dwfmm_plan plan, double lambda, const double* f, double
  * ||r|| <= rtol ||f|| and breakdown p^T A p == 0 are decided on the GPU), so
  * it never synchronises and solves on different plans and streams overlap;
  * the matvec uses the plan's precision.  dwfmm_cg_poll never blocks: *ready
- * = 1 once the work of the last dwfmm_cg_step has finished, and then status
+ * = 1 once the work of the last dwfmm_cg_step (or dwfmm_batch_cg_step) since
+ * the last dwfmm_cg_begin has finished (0 before the first), and then status
  * (R int32: 0 running, 1 converged, 2 breakdown), iters (R int32) and rr (R
  * doubles, ||r||^2) describe that point (any may be NULL).
  * dwfmm_cg_result copies the current c (host or device, ld >= N; a host

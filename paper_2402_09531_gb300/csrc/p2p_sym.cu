@@ -235,17 +235,18 @@ __global__ void __launch_bounds__(kSymThreads, 1) k_near_sym_tc(SymArgs a) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t bars[32];
   __shared__ uint32_t tmem_slot;
-  uint64_t* full = bars;            // [3] TMA landed
-  uint64_t* sfree = bars + 3;       // [3] stage consumed (16 warps + MMA commit)
-  uint64_t* efull = bars + 6;       // [2] E tile written (16 warps)
-  uint64_t* efree = bars + 8;       // [2] E tile read by the MMAs (commit)
-  uint64_t* tfull = bars + 10;      // [2] transposed accumulator complete (commit)
-  uint64_t* tempty = bars + 12;     // [2] transposed accumulator drained (16 warps)
-  uint64_t* cready = bars + 14;     // [2] lo rows combined into shared memory (8 warps)
-  uint64_t* ffull = bars + 16;      // [2] forward accumulators of an entry complete (commit)
-  uint64_t* fempty = bars + 18;     // [2] forward accumulators folded (16 warps)
-  uint64_t* qfull = bars + 20;      // q_T landed
-  uint64_t* fin = bars + 21;        // every MMA done
+  uint64_t* full = bars;                    // [kStages] TMA landed
+  uint64_t* sfree = full + kStages;         // [kStages] stage consumed (16 warps + MMA commit)
+  uint64_t* efull = sfree + kStages;        // [2] E tile written (16 warps)
+  uint64_t* efree = efull + 2;              // [2] E tile read by the MMAs (commit)
+  uint64_t* tfull = efree + 2;              // [2] transposed accumulator complete (commit)
+  uint64_t* tempty = tfull + 2;             // [2] transposed accumulator drained (16 warps)
+  uint64_t* cready = tempty + 2;            // [2] lo rows combined into shared memory (8 warps)
+  uint64_t* ffull = cready + 2;             // [2] forward accumulators of an entry complete (commit)
+  uint64_t* fempty = ffull + 2;             // [2] forward accumulators folded (16 warps)
+  uint64_t* qfull = fempty + 2;             // q_T landed
+  uint64_t* fin = qfull + 1;                // every MMA done
+  static_assert(2 * kStages + 16 <= 32, "barrier array");
 
   const int ld = a.ld;
   const int NT = ld / 128;                    // 128-target tiles
@@ -689,19 +690,20 @@ __global__ void __launch_bounds__(kSymThreads, 1) k_near_sym_gtc(SymGArgs a) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t bars[32];
   __shared__ uint32_t tmem_slot;
-  uint64_t* full = bars;            // [3] TMA landed (coordinates + charges of a chunk)
-  uint64_t* sfree = bars + 3;       // [3] stage read by the MMAs
-  uint64_t* efull = bars + 6;       // [2] E tile written (16 warps)
-  uint64_t* efree = bars + 8;       // [2] E tile read by the MMAs
-  uint64_t* tfull = bars + 10;      // [2] transposed accumulator complete
-  uint64_t* tempty = bars + 12;     // [2] transposed accumulator drained (16 warps)
-  uint64_t* cready = bars + 14;     // [2] lo rows combined (8 warps)
-  uint64_t* ffull = bars + 16;      // [2] forward accumulators of an entry complete
-  uint64_t* fempty = bars + 18;     // [2] forward accumulators folded (16 warps)
-  uint64_t* gfull = bars + 20;      // [2] G of a chunk complete
-  uint64_t* gfree = bars + 22;      // [2] G read by the compute warps (16 warps)
-  uint64_t* qfull = bars + 24;      // q_T and 2x'_T landed
-  uint64_t* fin = bars + 25;
+  uint64_t* full = bars;                    // [kStages] TMA landed (coordinates + charges of a chunk)
+  uint64_t* sfree = full + kStages;         // [kStages] stage read by the MMAs
+  uint64_t* efull = sfree + kStages;        // [2] E tile written (16 warps)
+  uint64_t* efree = efull + 2;              // [2] E tile read by the MMAs
+  uint64_t* tfull = efree + 2;              // [2] transposed accumulator complete
+  uint64_t* tempty = tfull + 2;             // [2] transposed accumulator drained (16 warps)
+  uint64_t* cready = tempty + 2;            // [2] lo rows combined (8 warps)
+  uint64_t* ffull = cready + 2;             // [2] forward accumulators of an entry complete
+  uint64_t* fempty = ffull + 2;             // [2] forward accumulators folded (16 warps)
+  uint64_t* gfull = fempty + 2;             // [2] G of a chunk complete
+  uint64_t* gfree = gfull + 2;              // [2] G read by the compute warps (16 warps)
+  uint64_t* qfull = gfree + 2;              // q_T and 2x'_T landed
+  uint64_t* fin = qfull + 1;
+  static_assert(2 * kStages + 20 <= 32, "barrier array");
 
   const int ld = a.ld;              // 256: two 128-target tiles, four 64-source chunks
   constexpr int NT = 2, NC = 4;

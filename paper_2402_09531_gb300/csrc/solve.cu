@@ -361,6 +361,7 @@ void cg_begin(Plan& P, double lam, const double* f, int R, int64_t ld, double rt
   S.lam = lam;
   S.rtol = rtol;
   S.active = true;
+  S.stepped = false;   // the previous status snapshot belongs to the previous solve
   P.cg_r.alloc(nr);
   P.cg_p.alloc(nr);
   P.cg_ap.alloc(nr);

@@ -287,3 +287,24 @@ def test_batched_server_same_within_tolerance_alone_and_in_the_mix():
         for c in (res[rid].c[0], r_alone[rid].c[0]):
             assert np.linalg.norm(r.f[0] - A(c)) / fn <= 2e-6
         assert np.linalg.norm(A(res[rid].c[0] - r_alone[rid].c[0])) / fn <= 4e-6
+
+
+def test_poll_after_a_new_begin_waits_for_its_first_step():
+    """A plan reused for a new solve must not report the previous solve's
+    status: after dwfmm_cg_begin the poll is not ready until a step ran."""
+    import torch
+    reqs = _requests([1100], seed0=95)
+    plans, fs = _mixed_plans(reqs)
+    p, f = plans[0], fs[0]
+    p.cg_begin(1e-1, f, rtol=1e-6)
+    p.cg_step(8)
+    torch.cuda.synchronize()
+    assert p.cg_poll()[0]
+    p.cg_begin(1e-1, f, rtol=1e-6)
+    torch.cuda.synchronize()
+    assert not p.cg_poll()[0]
+    p.cg_step(4)
+    torch.cuda.synchronize()
+    ready, st, it, rr = p.cg_poll()
+    assert ready and int(it[0]) <= 4
+    p.close()
