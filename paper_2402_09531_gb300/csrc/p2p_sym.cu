@@ -66,7 +66,7 @@ using namespace tc;
 constexpr int kSymCompWarps = 16;
 constexpr int kSymThreads = (kSymCompWarps + 2) * 32;
 constexpr int kChunk = 64;          // sources per chunk
-constexpr int kStages = 3;          // TMA stages (coordinates + FP16 charges of one chunk)
+constexpr int kStages = 4;          // TMA stages (coordinates + FP16 charges of one chunk)
 constexpr int kTmemCols = 256;      // forward 2 entries x 2 tiles x 32, transposed 2 x 32
 constexpr int kQChunkBytes = kChunk * 16 * 2 * 2;   // [s/8][4 cores][128 B]: 4 KB
 
@@ -781,7 +781,7 @@ __global__ void __launch_bounds__(kSymThreads, 1) k_near_sym_gtc(SymGArgs a) {
       if (bad) atomicExch(a.err, 3);
     }
   } else if (warp == kSymCompWarps) {
-    // ---- MMA issuer: G of chunk i + 1 ahead of the products of chunk i
+    // ---- MMA issuer: G of chunk i + 2 ahead of the products of chunk i
     if (lane == 0) {
       bool bad = !wait_sleep(qfull, 0u);
       const uint32_t ebase = sptr(ebuf), sbase = sptr(stages), qtb = sptr(qT), xtb = sptr(xT);
@@ -812,15 +812,19 @@ __global__ void __launch_bounds__(kSymThreads, 1) k_near_sym_gtc(SymGArgs a) {
         mma_commit(&gfull[gb]);
         return true;
       };
+      // G runs two chunks ahead of the products: G(i + 2) goes into the
+      // buffer of G(i) as soon as the compute warps have read G(i), so the
+      // products never wait on a G still queued behind other MMAs
       int jt = 0;
       if (nchunks > 0 && !bad) bad = !issue_g(0);
+      if (nchunks > 1 && !bad) bad = !issue_g(1);
       int i = 0;
       for (int e = 0; e < ne && !bad; ++e) {
         const int S = a.ups[e0 + e];
         const bool diag = S == T;
         const int fb = e & 1;
         for (int c = 0; c < NC; ++c, ++i) {
-          if (i + 1 < nchunks && !issue_g(i + 1)) {
+          if (i + 2 < nchunks && !issue_g(i + 2)) {
             bad = true;
             break;
           }
