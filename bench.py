@@ -283,6 +283,40 @@ def p2p_accounting(engine: str, pairs: int, diag: int, d: int, R: int):
             "kernel": "p2p (near field): k_sum_f32, evaluation and contraction on the FP32 pipe"}
 
 
+def phase_rooflines(iso_ms: dict, N: int, R: int, d: int, n: int, n_far: int, depth: int, evals_p2p: int,
+                    fp32_peak: float, hbm_peak: float) -> dict:
+    """Per-phase algorithmic work over the phase's isolated time, against the
+    peak that applies to it.  Models (stated per phase):
+      p2p      kernel evaluations x (3d + 4) flops, FP32 peak (contraction on
+               the tensor cores, not counted here)
+      m2l      n^2 node pairs per far block x (3d + 4) flops, FP32 peak
+      p2m_m2m  2 N n R (leaf moments) + (C - 1) 2 n^2 R (transfers to the
+               parents) flops, FP32 peak
+      l2l_l2p  the same count for the downward pass and the evaluation at the
+               sites, FP32 peak
+      gather   N R (8 + 4) bytes (float64 in, float32 leaf blocks out), HBM peak
+      scatter  N R (2 x 4 + 8) bytes (near and far float32 in, float64 out), HBM peak"""
+    C = (1 << (depth + 1)) - 1
+    work = {
+        "p2p": (evals_p2p * (3 * d + 4), "flop", fp32_peak, "TFLOP/s"),
+        "m2l": (n_far * n * n * (3 * d + 4), "flop", fp32_peak, "TFLOP/s"),
+        "p2m_m2m": (2 * N * n * R + (C - 1) * 2 * n * n * R, "flop", fp32_peak, "TFLOP/s"),
+        "l2l_l2p": (2 * N * n * R + (C - 1) * 2 * n * n * R, "flop", fp32_peak, "TFLOP/s"),
+        "gather": (N * R * 12, "byte", hbm_peak, "GB/s"),
+        "scatter": (N * R * 16, "byte", hbm_peak, "GB/s"),
+    }
+    out = {}
+    for k, (amount, kind, peak, unit) in work.items():
+        ms = iso_ms.get(k)
+        if not ms:
+            continue
+        scale = 1e12 if unit == "TFLOP/s" else 1e9
+        achieved = amount / (ms / 1e3) / scale
+        out[k] = {"ms": ms, "algorithmic": amount, "kind": kind, "achieved": achieved, "peak": peak,
+                  "unit": unit, "frac": achieved / peak}
+    return out
+
+
 def kernel_source_sha(src: str) -> str:
     import hashlib
     with open(os.path.join(ROOT, "paper_2402_09531_gb300", "csrc", src), "rb") as fh:
@@ -508,6 +542,8 @@ def run_ours(args):
                          "peak_basis": f"{sms} SMs x {FP32_LANES} FP32 lanes x 2 flop x {clock_mhz:.0f} MHz "
                                        f"(derived: no measured FP32 peak)"},
             "phase_ms_isolated": {k: v[0] / 2 for k, v in iso.items()},
+            "phase_roofline": phase_rooflines({k: v[0] / 2 for k, v in iso.items()}, N, R, d, n_x, n_far, depth,
+                                              acct["evals"], peak, float(peaks.get("hbm_gbs", 6804.8))),
             "phase_ms_concurrent": {"note": "timed steps; the far-field phases run on the caller's stream "
                                             "while the near field occupies the GPU from a second stream, so "
                                             "their times include waiting for it",
@@ -569,14 +605,15 @@ def _serve_poisson(reqs, precision, lam, loads=(0.5, 0.8, 1.0), seed=7, batched=
     return out
 
 
-def _sample_requests(count, nmax):
-    """The first `count` requests of the serving stream with N <= nmax (eta=2,
-    Sec. 6.2 weights: the readings for the stream's unstated parameters)."""
+def _sample_requests(count, nmax, nmin=0):
+    """The first `count` requests of the serving stream with nmin <= N <= nmax
+    (eta=2, Sec. 6.2 weights: the readings for the stream's unstated
+    parameters)."""
     import dwfmm_inputs as di
     from paper_2402_09531_gb300.serving import Request
     reqs = []
     for w in di.serving_requests(2000):
-        if w.n > nmax:
+        if w.n > nmax or w.n < nmin:
             continue
         X, f = di.sites_and_rhs(w, nrhs=1)
         reqs.append(Request(rid=len(reqs), X=X, f=f, kernel=w.kernel, gamma=w.gamma, q=w.q, eta=2.0,
@@ -799,12 +836,60 @@ def run_batch(args):
         "batch_ms": ms_batch, "batch_pts_rhs_per_s": units / (ms_batch / 1e3),
         "sequential_ms": ms_seq, "sequential_pts_rhs_per_s": units / (ms_seq / 1e3),
         "speedup": ms_seq / ms_batch, "tree_builds_s": build_s, "batch_create_s": create_s,
-        "launch_shape": "one launch per right-hand-side class" if info["split"] else "one padded launch",
+        "launch_shape": {
+            k: f"{info[k]['threads']} threads per CTA, "
+               + ("one launch per right-hand-side class" if info[k]["per_class"] else "one padded launch")
+            for k in ("near_shape", "m2l_shape")},
         "autotune_ms": info["tune_ms"], "leaves": info["leaves"],
         "l2": "flushed between steps (512 MiB write)"}), flush=True)
     b.close()
     for p in plans:
         p.close()
+
+
+def run_serve_large(args):
+    """The serving stream at larger N: the first requests with N in
+    [serve_nmin, serve_nmax], float64, lambda = 1e-6, rtol = 1e-6, all
+    arriving at t = 0, 8 active slots; p50/p99, solves/s and, per request,
+    iterations and time per iteration, from which the largest requests of
+    the stream (N = 5e5) are extrapolated (stated as such)."""
+    import numpy as np
+    import torch
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2402_09531_gb300.serving import Server, summarize
+    torch.cuda.set_device(0)
+    reqs = _sample_requests(args.serve_count, args.serve_nmax, args.serve_nmin)
+    srv = Server(precision="fp64", max_active=8)
+    srv.run(reqs[:1])
+    t0 = time.perf_counter()
+    res = srv.run(reqs)
+    wall = time.perf_counter() - t0
+    out = summarize(res, wall)
+    srv.close()
+    per = []
+    byid = {r.rid: r for r in reqs}
+    for r in res:
+        n = byid[r.rid].X.shape[0]
+        busy = (r.t_done - r.t_admit) * 1e3
+        per.append({"n": n, "iters": r.iters, "status": r.status, "latency_ms": r.latency_ms,
+                    "ms_per_iter_in_mix": busy / max(1, r.iters)})
+    out.update({"workload": f"serving stream, N in [{args.serve_nmin}, {args.serve_nmax}], float64, lambda = 1e-6",
+                "requests_detail": sorted(per, key=lambda x: x["n"])})
+    ok = [p for p in per if p["status"] == "ok"]
+    if len(ok) >= 3:
+        ns = np.array([p["n"] for p in ok], float)
+        it = np.array([p["iters"] for p in ok], float)
+        ms = np.array([p["ms_per_iter_in_mix"] for p in ok], float)
+        a_it, b_it = np.polyfit(np.log(ns), np.log(it), 1)
+        a_ms, b_ms = np.polyfit(np.log(ns), np.log(ms), 1)
+        n5 = 5e5
+        out["extrapolated_n5e5"] = {"iterations": float(np.exp(b_it) * n5 ** a_it),
+                                    "ms_per_iter": float(np.exp(b_ms) * n5 ** a_ms),
+                                    "solve_s": float(np.exp(b_it) * n5 ** a_it * np.exp(b_ms) * n5 ** a_ms / 1e3),
+                                    "fit": f"iters ~ N^{a_it:.2f}, ms/iter ~ N^{a_ms:.2f} (in an 8-way mix)",
+                                    "note": "power laws through the served requests; not measured at N = 5e5"}
+    print(json.dumps(out), flush=True)
 
 
 def run_reference(args):
@@ -847,6 +932,11 @@ def main():
     ap.add_argument("--sweep-requests", type=int, default=32)
     ap.add_argument("--sweep-nmax", type=int, default=3000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-large", action="store_true",
+                    help="float64 lambda = 1e-6 serving at larger N, with an extrapolation to N = 5e5")
+    ap.add_argument("--serve-nmin", type=int, default=8000)
+    ap.add_argument("--serve-nmax", type=int, default=30000)
+    ap.add_argument("--serve-count", type=int, default=8)
     ap.add_argument("--batch", action="store_true",
                     help="the 256-problem batching workload: fused batch matvec against one matvec per problem")
     ap.add_argument("--batch-count", type=int, default=256)
@@ -867,6 +957,8 @@ def main():
         run_cfg2_solve(args)
     elif args.batch:
         run_batch(args)
+    elif args.serve_large:
+        run_serve_large(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

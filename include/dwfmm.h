@@ -256,22 +256,33 @@ dwfmm_status dwfmm_evaluate(dwfmm_plan plan, const double* targets, int64_t nt, 
  * the number of right-hand sides of problem i for every later call.  The
  * near field of all problems is one launch of the kernel-summation engine,
  * the couplings (M2L) of all problems another, the upward and downward
- * passes one launch per tree height/level; the launch shape of the two fused
- * launches (one padded launch or one per right-hand-side class) is chosen by
- * timing both once, and the whole sequence is captured as a CUDA graph.
+ * passes one launch per tree height/level; the launch shape of each of the
+ * two fused launches (CTA width; one padded launch or one per right-hand-side
+ * class) is chosen by timing every candidate on the batch's data, and the
+ * whole sequence is captured as a CUDA graph.
  * The plans must stay alive and keep their trees while the batch exists.
  * Synchronises `stream` before it starts.
  * dwfmm_batch_matvec: y[i] = K_tilde_i x[i] for every problem, x[i] and y[i]
  * device buffers, column-major N_i x nrhs[i] with leading dimension N_i;
  * enqueued on `stream` (one graph launch).
- * dwfmm_batch_info: split (1 if one launch per class was faster), tune_ms
- * (2 doubles: padded, per class) and the total number of leaves.
+ * dwfmm_batch_info: split (1 if the near field runs one launch per class),
+ * tune_ms (2 doubles: near field + couplings at their best padded shapes, and
+ * at their best shapes with per-class launches allowed) and the total number
+ * of leaves; any output pointer may be NULL.
  * Errors: INVALID_ARG, STATE (a plan without a tree), OOM, CUDA. */
 typedef struct dwfmm_batch_s* dwfmm_batch;
 dwfmm_status dwfmm_batch_create(const dwfmm_plan* plans, const int32_t* nrhs, int32_t count, void* stream,
                                 dwfmm_batch* out);
 dwfmm_status dwfmm_batch_matvec(dwfmm_batch batch, const double* const* x, double* const* y, void* stream);
 dwfmm_status dwfmm_batch_info(dwfmm_batch batch, int32_t* split, double* tune_ms, int64_t* leaves);
+
+/* Launch shapes the batch's autotuner chose at creation (every candidate
+ * timed on the batch's own data): shape[0] 1 if the near field runs one
+ * launch per right-hand-side class, shape[1] its threads per CTA (each
+ * thread owns 2 targets per pass: 32, 64, 96 or 128), shape[2], shape[3]
+ * the same for the couplings (M2L).  `shape` is a host array of 4 int32.
+ * Errors: INVALID_ARG (NULL batch or shape).  No counterpart in the paper. */
+dwfmm_status dwfmm_batch_shape(dwfmm_batch batch, int32_t* shape);
 
 /* Batched CG (Sec. 2, Eq. (2.2); the CG of Sec. 6.2): `iters` iterations of
  * the incremental CG of every problem of the batch, each begun with

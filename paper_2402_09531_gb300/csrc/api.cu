@@ -738,6 +738,12 @@ dwfmm_status dwfmm_batch_info(dwfmm_batch batch, int32_t* split, double* tune_ms
   return DWFMM_OK;
 }
 
+dwfmm_status dwfmm_batch_shape(dwfmm_batch batch, int32_t* shape) {
+  if (!batch || !shape) return DWFMM_ERR_INVALID_ARG;
+  dw::batch_shape(*batch->B, shape);
+  return DWFMM_OK;
+}
+
 dwfmm_status dwfmm_batch_destroy(dwfmm_batch batch) {
   if (!batch) return DWFMM_OK;
   dw::batch_delete(batch->B);

@@ -40,8 +40,13 @@ struct Batch {
     int RC, leaf_first, leaf_count, clus_first, clus_count;
   };
   std::vector<Cls> classes;
-  bool split = false;
-  double tune_ms[2] = {0, 0};
+  bool split = false;            // near field: one launch per right-hand-side class
+  double tune_ms[2] = {0, 0};    // best padded / best per-class time of near field + couplings
+  // tile shapes chosen by the autotuner: CTA width (targets per pass = 2 x
+  // threads) and right-hand-side grouping, separately for the fused near
+  // field and the fused couplings
+  int thr_near = 0, thr_m2l = 0;
+  bool split_m2l = false;
   cudaStream_t stream = nullptr, side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_copy = nullptr;
   bool copied = false;
@@ -132,33 +137,35 @@ SumArgs m2l_args(Batch& B, int RC, int clus_first) {
 
 int threads_for(int ld) { return std::min(128, round_up((ld + 1) / 2, 32)); }
 
-// The fused near-field work: interleave charges, P2P launch(es).
-void enqueue_near(Batch& B, bool split, cudaStream_t s) {
+// The fused near-field work: interleave charges, P2P launch(es) with
+// `threads` per CTA.
+void enqueue_near(Batch& B, bool split, int threads, cudaStream_t s) {
   if (!split) {
     launch_interleave(B.xb.p, B.Ltot, B.ld, B.RCmax, B.xq.p, s);
-    launch_sum_f32(B.D, B.kernel, B.RCmax, p2p_args(B, B.RCmax, 0), B.Ltot, threads_for(B.ld),
+    launch_sum_f32(B.D, B.kernel, B.RCmax, p2p_args(B, B.RCmax, 0), B.Ltot, threads,
                    sum_stage_bytes(B.D, B.RCmax, B.ld), s);
     return;
   }
   for (const auto& c : B.classes) {
     launch_interleave(B.xb.p + static_cast<int64_t>(c.leaf_first) * kRC * B.ld, c.leaf_count, B.ld, c.RC,
                       B.xq.p + static_cast<int64_t>(c.leaf_first) * B.ld * c.RC, s);
-    launch_sum_f32(B.D, B.kernel, c.RC, p2p_args(B, c.RC, c.leaf_first), c.leaf_count, threads_for(B.ld),
+    launch_sum_f32(B.D, B.kernel, c.RC, p2p_args(B, c.RC, c.leaf_first), c.leaf_count, threads,
                    sum_stage_bytes(B.D, c.RC, B.ld), s);
   }
 }
 
-void enqueue_m2l(Batch& B, bool split, cudaStream_t s) {
+// The fused couplings (M2L) with `threads` per CTA.
+void enqueue_m2l(Batch& B, bool split, int threads, cudaStream_t s) {
   if (!split) {
     launch_interleave(B.mom.p, B.Ctot, B.n_pad, B.RCmax, B.momq.p, s);
-    launch_sum_f32(B.D, B.kernel, B.RCmax, m2l_args(B, B.RCmax, 0), B.Ctot, threads_for(B.n_pad),
+    launch_sum_f32(B.D, B.kernel, B.RCmax, m2l_args(B, B.RCmax, 0), B.Ctot, threads,
                    sum_stage_bytes(B.D, B.RCmax, B.n_pad), s);
     return;
   }
   for (const auto& c : B.classes) {
     launch_interleave(B.mom.p + static_cast<int64_t>(c.clus_first) * kRC * B.n_pad, c.clus_count, B.n_pad, c.RC,
                       B.momq.p + static_cast<int64_t>(c.clus_first) * B.n_pad * c.RC, s);
-    launch_sum_f32(B.D, B.kernel, c.RC, m2l_args(B, c.RC, c.clus_first), c.clus_count, threads_for(B.n_pad),
+    launch_sum_f32(B.D, B.kernel, c.RC, m2l_args(B, c.RC, c.clus_first), c.clus_count, threads,
                    sum_stage_bytes(B.D, c.RC, B.n_pad), s);
   }
 }
@@ -168,11 +175,11 @@ void enqueue_matvec(Batch& B) {
   launch_gather_batched(B.probs.p, B.d_leaf_off.p, B.P, B.Ltot, B.ld, B.xb.p, s);
   DW_CUDA(cudaEventRecord(B.ev_fork, s));
   DW_CUDA(cudaStreamWaitEvent(B.side, B.ev_fork, 0));
-  enqueue_near(B, B.split, B.side);
+  enqueue_near(B, B.split, B.thr_near, B.side);
   DW_CUDA(cudaEventRecord(B.ev_join, B.side));
   for (size_t h = 0; h < B.up_off.size(); ++h)
     launch_moments_batched(B.probs.p, B.work.p + B.up_off[h], B.up_cnt[h], B.far_smem, s);
-  enqueue_m2l(B, B.split, s);
+  enqueue_m2l(B, B.split_m2l, B.thr_m2l, s);
   for (size_t j = 0; j < B.down_off.size(); ++j)
     launch_downward_batched(B.probs.p, B.work.p + B.down_off[j], B.down_cnt[j], B.far_smem, s);
   DW_CUDA(cudaStreamWaitEvent(s, B.ev_join, 0));
@@ -180,15 +187,17 @@ void enqueue_matvec(Batch& B) {
   DW_CUDA(cudaGetLastError());
 }
 
-double time_shape(Batch& B, bool split) {
+// Best of two timed runs of one launch shape of the near field (which = 0)
+// or the couplings (which = 1).
+double time_shape(Batch& B, int which, bool split, int threads) {
   cudaEvent_t a, b;
   DW_CUDA(cudaEventCreate(&a));
   DW_CUDA(cudaEventCreate(&b));
   float best = 1e30f;
   for (int rep = 0; rep < 2; ++rep) {
     DW_CUDA(cudaEventRecord(a, B.stream));
-    enqueue_near(B, split, B.stream);
-    enqueue_m2l(B, split, B.stream);
+    if (which == 0) enqueue_near(B, split, threads, B.stream);
+    else enqueue_m2l(B, split, threads, B.stream);
     DW_CUDA(cudaEventRecord(b, B.stream));
     DW_CUDA(cudaEventSynchronize(b));
     float ms = 0.f;
@@ -198,6 +207,46 @@ double time_shape(Batch& B, bool split) {
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   return best;
+}
+
+// Autotuner: every candidate shape (CTA width 32, 64, 128 threads up to the
+// widest useful one for the group's slots, and that one; one padded launch
+// or one per right-hand-side class) of the near field and of the couplings
+// is timed on the batch's own data, and the fastest of each is kept.  Each
+// thread sums its targets' sources in the same order whatever the width,
+// so the choice changes no result.
+void tune_shapes(Batch& B) {
+  const bool can_split = B.classes.size() > 1;
+  double best_pad = 0.0, best_split = 0.0;
+  for (int which = 0; which < 2; ++which) {
+    const int widest = threads_for(which == 0 ? B.ld : B.n_pad);
+    double best = 1e30, bp = 1e30, bs = 1e30;
+    bool bsplit = false;
+    int bthr = widest;
+    for (int thr = 32; thr <= widest; thr = (thr * 2 > widest && thr < widest) ? widest : thr * 2) {
+      for (int sp = 0; sp < (can_split ? 2 : 1); ++sp) {
+        const double ms = time_shape(B, which, sp != 0, thr);
+        if (sp) bs = std::min(bs, ms);
+        else bp = std::min(bp, ms);
+        if (ms < best) {
+          best = ms;
+          bsplit = sp != 0;
+          bthr = thr;
+        }
+      }
+    }
+    if (which == 0) {
+      B.split = bsplit;
+      B.thr_near = bthr;
+    } else {
+      B.split_m2l = bsplit;
+      B.thr_m2l = bthr;
+    }
+    best_pad += bp;
+    best_split += can_split ? bs : bp;
+  }
+  B.tune_ms[0] = best_pad;
+  B.tune_ms[1] = best_split;
 }
 
 }  // namespace
@@ -377,9 +426,7 @@ void batch_create(Batch& B, Plan* const* plans, const int32_t* nrhs, int count) 
   }
   DW_CUDA(cudaStreamSynchronize(s));
   // autotune the P2P/M2L launch shape, then capture the whole matvec
-  B.tune_ms[0] = time_shape(B, false);
-  B.tune_ms[1] = B.classes.size() > 1 ? time_shape(B, true) : B.tune_ms[0];
-  B.split = B.classes.size() > 1 && B.tune_ms[1] < B.tune_ms[0];
+  tune_shapes(B);
   DW_CUDA(cudaStreamBeginCapture(B.stream, cudaStreamCaptureModeThreadLocal));
   enqueue_matvec(B);
   DW_CUDA(cudaStreamEndCapture(B.stream, &B.graph));
@@ -414,6 +461,13 @@ void batch_delete(Batch* b) {
   b->release();
   delete b;
 }
+void batch_shape(const Batch& B, int32_t* shape) {
+  shape[0] = B.split ? 1 : 0;
+  shape[1] = B.thr_near;
+  shape[2] = B.split_m2l ? 1 : 0;
+  shape[3] = B.thr_m2l;
+}
+
 void batch_info(const Batch& B, int32_t* split, double* tune_ms, int64_t* leaves) {
   if (split) *split = B.split ? 1 : 0;
   if (tune_ms) {

@@ -375,6 +375,7 @@ void batch_delete(Batch* b);
 void batch_create(Batch& B, Plan* const* plans, const int32_t* nrhs, int count);
 void batch_matvec(Batch& B, const double* const* x, double* const* y, cudaStream_t s);
 void batch_info(const Batch& B, int32_t* split, double* tune_ms, int64_t* leaves);
+void batch_shape(const Batch& B, int32_t* shape);
 dwfmm_status direct_sum_noalloc(int kernel, double sigma, const double* pts, int64_t n, int d, int64_t ldp,
                                 const double* x, double* y, int R, int64_t ldx, int64_t ldy,
                                 cudaStream_t s);

@@ -36,7 +36,8 @@ EXPORTS = ("dwfmm_plan_create", "dwfmm_plan_set_nodes", "dwfmm_tree_build", "dwf
            "dwfmm_set_profiling", "dwfmm_phase_times", "dwfmm_direct_sum_noalloc",
            "dwfmm_cg_begin", "dwfmm_cg_step", "dwfmm_cg_poll", "dwfmm_cg_result", "dwfmm_residual",
            "dwfmm_refine",
-           "dwfmm_batch_create", "dwfmm_batch_matvec", "dwfmm_batch_info", "dwfmm_batch_cg_step",
+           "dwfmm_batch_create", "dwfmm_batch_matvec", "dwfmm_batch_info", "dwfmm_batch_shape",
+           "dwfmm_batch_cg_step",
            "dwfmm_batch_destroy",
            "dwfmm_evaluate")
 
@@ -89,6 +90,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "dwfmm_batch_matvec": (i32, [P, P, P, P]),
         "dwfmm_batch_info": (i32, [P, C.POINTER(i32), P, C.POINTER(i64)]),
         "dwfmm_batch_cg_step": (i32, [P, i32, P]),
+        "dwfmm_batch_shape": (i32, [P, P]),
         "dwfmm_batch_destroy": (i32, [P]),
         "dwfmm_evaluate": (i32, [P, P, i64, i64, P, i64, P, i64, i32, P]),
     }
@@ -427,7 +429,11 @@ class Batch:
         tune = (C.c_double * 2)()
         leaves = C.c_int64(0)
         self._l.dwfmm_batch_info(self.h, C.byref(split), tune, C.byref(leaves))
-        return {"split": bool(split.value), "tune_ms": [tune[0], tune[1]], "leaves": int(leaves.value)}
+        shape = (C.c_int32 * 4)()
+        self._l.dwfmm_batch_shape(self.h, shape)
+        return {"split": bool(split.value), "tune_ms": [tune[0], tune[1]], "leaves": int(leaves.value),
+                "near_shape": {"per_class": bool(shape[0]), "threads": int(shape[1])},
+                "m2l_shape": {"per_class": bool(shape[2]), "threads": int(shape[3])}}
 
     def close(self):
         if getattr(self, "h", None):

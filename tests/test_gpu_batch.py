@@ -47,6 +47,11 @@ def test_batch_equals_single_problem_matvecs():
     torch.cuda.synchronize()
     info = b.info()
     assert info["leaves"] == sum(p.info()[3] >= 0 and 2 ** p.info()[3] for p in plans)
+    # the autotuner picked one timed shape for each fused launch
+    for k in ("near_shape", "m2l_shape"):
+        assert info[k]["threads"] in (32, 64, 96, 128), info
+    assert info["split"] == info["near_shape"]["per_class"]
+    assert 0 < min(info["tune_ms"])
     for i, p in enumerate(plans):
         ref = torch.empty_like(xs[i])
         p.matvec(xs[i], ref)
