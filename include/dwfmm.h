@@ -323,6 +323,18 @@ dwfmm_status dwfmm_plan_info(dwfmm_plan plan, int64_t* n_x, int64_t* n_far, int6
  * the Gaussian's exponent 2x'.s' also on the tensor cores. */
 dwfmm_status dwfmm_near_engine(dwfmm_plan plan, int32_t* engine);
 
+/* Which engine ran the expansion phases (P2M, M2M, L2L, L2P and the V^{-T},
+ * V^{-1} transforms of Sec. 5.2, Eq. (5.4)) in the plan's last matvec
+ * (*engine, -1 before the first): 0 float64 CUDA cores; 1 float32 CUDA
+ * cores; 2 MIXED on the tensor cores: basis values and right-hand sides
+ * (scaled per column by a power of two) split into FP16 hi + lo,
+ * hi*hi + hi*lo + lo*hi accumulated in FP32 by tcgen05.mma, per-cluster
+ * contractions in 64-wide chunks folded in FP32, the transforms one GEMM per
+ * tree level with the constant V^{-1} tile.  MIXED plans take engine 2 when
+ * |Lambda| <= 128, leaves hold 128 or 256 sites and a multi-index has at
+ * most 20 nonzero entries; otherwise engine 1.  Errors: INVALID_ARG. */
+dwfmm_status dwfmm_far_engine(dwfmm_plan plan, int32_t* engine);
+
 /* Copy out plan data (host buffers, NULL to skip), for tests and tools:
  *  weights: d doubles; lam: n x d int32 multi-indices (row-major);
  *  nodes: n x d doubles; pivots: n int32 Halton indices (0-based, -1 if the

@@ -105,6 +105,9 @@ void Plan::free_all() {
   d_nodes.release();
   d_vinv.release();
   d_vinv32.release();
+  far_vt.release();
+  far_vexp.release();
+  far_vt_ok = false;
   d_err.release();
   stage_in.release();
   stage_out.release();
@@ -421,6 +424,12 @@ dwfmm_status dwfmm_plan_destroy(dwfmm_plan plan) {
 dwfmm_status dwfmm_near_engine(dwfmm_plan plan, int32_t* engine) {
   if (!plan || !engine) return DWFMM_ERR_INVALID_ARG;
   *engine = plan->P.near_engine;
+  return DWFMM_OK;
+}
+
+dwfmm_status dwfmm_far_engine(dwfmm_plan plan, int32_t* engine) {
+  if (!plan || !engine) return DWFMM_ERR_INVALID_ARG;
+  *engine = plan->P.far_engine;
   return DWFMM_OK;
 }
 

@@ -297,6 +297,12 @@ struct Plan {
   DBuf<uint16_t> sym_xa16, sym_xb16;   // FP16 hi/lo coordinate blocks (2x' and x') of the Gaussian path
   bool sym_x16_ok = false;
   int near_engine = -1;   // engine of the last near field (dwfmm_near_engine)
+  // tensor-core far field (MIXED): FP16 hi/lo tiles of V^{-T} and V^{-1}
+  // scaled by 2^-far_vexp, valid for the current node set
+  DBuf<uint16_t> far_vt;
+  DBuf<int> far_vexp;
+  bool far_vt_ok = false;
+  int far_engine = -1;    // engine of the last far field (dwfmm_far_engine)
   cudaEvent_t ev_scaled = nullptr;
   DBuf<int> d_err;   // device error flag (3 = a bounded wait timed out)
 
@@ -329,6 +335,8 @@ size_t farfield_smem_need(const Plan& P, bool fp64);
 void launch_gather(Plan& P, const double* x, int64_t ldx, int r0, int Rc, bool fp64);
 void launch_scatter(Plan& P, double* y, int64_t ldy, int r0, int Rc, bool fp64);
 void launch_farfield(Plan& P, int Rc, bool fp64);
+bool farfield_tc_eligible(const Plan& P);   // farfield_tc.cu
+void farfield_tc(Plan& P, int Rc);
 void launch_m2l(Plan& P, int Rc, bool fp64);
 void launch_nearfield(Plan& P, int Rc, bool fp64, cudaStream_t s);
 // Bit of the current device in a per-device mask (kernel attributes are set

@@ -379,8 +379,15 @@ void farfield_impl(Plan& P, int Rc) {
   const int64_t ny = static_cast<int64_t>(L) * kRC * P.m_pad;
   if (P.jmin > J) {  // no admissible block: the far field is empty
     DW_CUDA(cudaMemsetAsync(B.yfar, 0, ny * sizeof(T), s));
+    P.far_engine = sizeof(T) == 8 ? 0 : 1;
     return;
   }
+  if (sizeof(T) == 4 && farfield_tc_eligible(P)) {
+    P.far_engine = 2;
+    farfield_tc(P, Rc);
+    return;
+  }
+  P.far_engine = sizeof(T) == 8 ? 0 : 1;
   const size_t sm_mom = (static_cast<size_t>(kChunk) * e.lsum + kChunk * kRC + static_cast<size_t>(e.n_pad) * kRC) * sizeof(T);
   const size_t sm_down = (2 * static_cast<size_t>(e.n_pad) * kRC + static_cast<size_t>(kFarThreads) * e.lsum) * sizeof(T);
   timer_begin(P, 1, s);

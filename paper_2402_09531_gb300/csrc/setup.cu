@@ -380,6 +380,7 @@ void setup_vinv_from_nodes(Plan& P) {
   k_gauss_jordan<<<1, 1024, 0, s>>>(aug.p, P.n, err.p);
   P.d_vinv.alloc(static_cast<size_t>(P.n_pad) * P.n_pad);
   P.d_vinv32.alloc(static_cast<size_t>(P.n_pad) * P.n_pad);
+  P.far_vt_ok = false;
   k_extract_vinv<<<ceil_div(static_cast<int64_t>(P.n_pad) * P.n_pad, 256), 256, 0, s>>>(
       aug.p, P.n, P.n_pad, P.d_vinv.p, P.d_vinv32.p);
   DW_CUDA(cudaGetLastError());

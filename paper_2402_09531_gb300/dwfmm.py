@@ -32,7 +32,7 @@ PHASES = ("gather", "p2m_m2m", "m2l", "l2l_l2p", "p2p", "scatter", "matvec")
 # Every entry point declared in include/dwfmm.h.
 EXPORTS = ("dwfmm_plan_create", "dwfmm_plan_set_nodes", "dwfmm_tree_build", "dwfmm_matvec",
            "dwfmm_solve", "dwfmm_plan_destroy", "dwfmm_status_string", "dwfmm_last_error",
-           "dwfmm_plan_info", "dwfmm_near_engine", "dwfmm_plan_export", "dwfmm_tree_export", "dwfmm_lists_export",
+           "dwfmm_plan_info", "dwfmm_near_engine", "dwfmm_far_engine", "dwfmm_plan_export", "dwfmm_tree_export", "dwfmm_lists_export",
            "dwfmm_set_profiling", "dwfmm_phase_times", "dwfmm_direct_sum_noalloc",
            "dwfmm_cg_begin", "dwfmm_cg_step", "dwfmm_cg_poll", "dwfmm_cg_result", "dwfmm_residual",
            "dwfmm_refine",
@@ -74,6 +74,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "dwfmm_last_error": (C.c_char_p, [P]),
         "dwfmm_plan_info": (i32, [P, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), C.POINTER(i32)]),
         "dwfmm_near_engine": (i32, [P, C.POINTER(i32)]),
+        "dwfmm_far_engine": (i32, [P, C.POINTER(i32)]),
         "dwfmm_plan_export": (i32, [P, P, P, P, P, P]),
         "dwfmm_tree_export": (i32, [P, P, P, P, P, P]),
         "dwfmm_lists_export": (i32, [P, P, P]),
@@ -344,6 +345,14 @@ class Plan:
         e = C.c_int32(-1)
         self.check(self._l.dwfmm_near_engine(self.h, C.byref(e)))
         return self.NEAR_ENGINES.get(int(e.value), str(e.value))
+
+    FAR_ENGINES = {-1: "none", 0: "fp64_cuda_cores", 1: "fp32_cuda_cores", 2: "mixed_fp16_tensor"}
+
+    def far_engine(self) -> str:
+        """Engine that ran the expansion phases (P2M/M2M/L2L/L2P) in the last matvec."""
+        e = C.c_int32(-1)
+        self.check(self._l.dwfmm_far_engine(self.h, C.byref(e)))
+        return self.FAR_ENGINES.get(int(e.value), str(e.value))
 
     def export_expansion(self):
         n, d = self.n_x, self.d
