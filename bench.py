@@ -284,7 +284,7 @@ def p2p_accounting(engine: str, pairs: int, diag: int, d: int, R: int):
 
 
 def phase_rooflines(iso_ms: dict, N: int, R: int, d: int, n: int, n_far: int, depth: int, evals_p2p: int,
-                    fp32_peak: float, hbm_peak: float) -> dict:
+                    fp32_peak: float, hbm_peak: float, far_engine: str = "", tensor_peak: float = 0.0) -> dict:
     """Per-phase algorithmic work over the phase's isolated time, against the
     peak that applies to it.  Models (stated per phase):
       p2p      kernel evaluations x (3d + 4) flops, FP32 peak (contraction on
@@ -294,6 +294,10 @@ def phase_rooflines(iso_ms: dict, N: int, R: int, d: int, n: int, n_far: int, de
                parents) flops, FP32 peak
       l2l_l2p  the same count for the downward pass and the evaluation at the
                sites, FP32 peak
+      (far engine "mixed_fp16_tensor": p2m_m2m and l2l_l2p run as FP16 hi/lo
+      contractions on the tensor cores, three products per term: 3x those
+      flops against the dense FP16 tensor peak, the measured bf16 figure,
+      the same nominal rate)
       gather   N R (8 + 4) bytes (float64 in, float32 leaf blocks out), HBM peak
       scatter  N R (2 x 4 + 8) bytes (near and far float32 in, float64 out), HBM peak"""
     C = (1 << (depth + 1)) - 1
@@ -305,6 +309,11 @@ def phase_rooflines(iso_ms: dict, N: int, R: int, d: int, n: int, n_far: int, de
         "gather": (N * R * 12, "byte", hbm_peak, "GB/s"),
         "scatter": (N * R * 16, "byte", hbm_peak, "GB/s"),
     }
+    tensor = far_engine == "mixed_fp16_tensor" and tensor_peak > 0
+    if tensor:
+        for k in ("p2m_m2m", "l2l_l2p"):
+            amount = work[k][0]
+            work[k] = (3 * amount, "tensor flop", tensor_peak, "TFLOP/s")
     out = {}
     for k, (amount, kind, peak, unit) in work.items():
         ms = iso_ms.get(k)
@@ -314,6 +323,10 @@ def phase_rooflines(iso_ms: dict, N: int, R: int, d: int, n: int, n_far: int, de
         achieved = amount / (ms / 1e3) / scale
         out[k] = {"ms": ms, "algorithmic": amount, "kind": kind, "achieved": achieved, "peak": peak,
                   "unit": unit, "frac": achieved / peak}
+    if tensor:
+        for k in ("p2m_m2m", "l2l_l2p"):
+            if k in out:
+                out[k]["engine"] = "tcgen05 kind::f16, FP16 hi/lo, 3 products; one or two launches per tree level"
     return out
 
 
@@ -542,8 +555,10 @@ def run_ours(args):
                          "peak_basis": f"{sms} SMs x {FP32_LANES} FP32 lanes x 2 flop x {clock_mhz:.0f} MHz "
                                        f"(derived: no measured FP32 peak)"},
             "phase_ms_isolated": {k: v[0] / 2 for k, v in iso.items()},
+            "far_engine": plan.far_engine(),
             "phase_roofline": phase_rooflines({k: v[0] / 2 for k, v in iso.items()}, N, R, d, n_x, n_far, depth,
-                                              acct["evals"], peak, float(peaks.get("hbm_gbs", 6804.8))),
+                                              acct["evals"], peak, float(peaks.get("hbm_gbs", 6804.8)),
+                                              plan.far_engine(), float(peaks.get("bf16_tflops", 1900.0))),
             "phase_ms_concurrent": {"note": "timed steps; the far-field phases run on the caller's stream "
                                             "while the near field occupies the GPU from a second stream, so "
                                             "their times include waiting for it",
@@ -652,7 +667,8 @@ def run_solve_sample(args):
 
 def run_eta_sweep(args):
     """The bench workload (d = 10 Gaussian, N = 2^20, 16 RHS, mixed) with the
-    Sec. 6.2 weight rule at eta = 0.5 (the paper's value) and eta = 1:
+    Sec. 6.2 weight rule and with the bench's rule, each at eta = 0.5 (the
+    paper's value) and eta = 1:
     |Lambda|, far blocks, near pairs, matvec time (CUDA events, L2 flushed)
     and the compression error of the mixed matvec against the exact product
     on sampled rows (float64 evaluation of K[rows, :] x)."""
@@ -682,10 +698,12 @@ def run_eta_sweep(args):
     exact = exact.cpu().numpy()
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
-    out = {"workload": w.name, "weights": "Sec. 6.2 rule (tau_k^-1 = eta b_k, b_k = 2 gamma_k)",
+    out = {"workload": w.name,
+           "weights": {"paper_logrho": "Sec. 6.2 rule (tau_k^-1 = eta b_k, b_k = 2 gamma_k)",
+                       "inv_gamma": "omega_k = gamma_1 / gamma_k (the bench's rule)"},
            "rows_sampled": int(len(rows)), "etas": {}}
-    for eta in (0.5, 1.0):
-        plan = Plan(d=w.d, kernel=w.kernel, sigma=w.sigma, gamma=w.gamma, weight_rule="paper_logrho", q=w.q,
+    for rule, eta in (("paper_logrho", 0.5), ("paper_logrho", 1.0), ("inv_gamma", 0.5), ("inv_gamma", 1.0)):
+        plan = Plan(d=w.d, kernel=w.kernel, sigma=w.sigma, gamma=w.gamma, weight_rule=rule, q=w.q,
                     eta=eta, leaf_size=w.leaf, precision="mixed", max_rhs=w.nrhs)
         plan.tree_build(Xd)
         n_x, n_far, n_near, depth = plan.info()
@@ -709,7 +727,8 @@ def run_eta_sweep(args):
         plan.set_profiling(False)
         y = yd.cpu().numpy()[:, rows]
         col = np.linalg.norm(y - exact, axis=1) / np.linalg.norm(exact, axis=1)
-        out["etas"][str(eta)] = {
+        out["etas"][str(eta) if rule == "paper_logrho" else f"{eta} inv_gamma"] = {
+            "weight_rule": rule, "far_engine": plan.far_engine(),
             "n_x": n_x, "far_blocks": n_far, "near_blocks": n_near, "depth": depth,
             "near_pairs": pairs, "near_fraction": pairs / float(w.n) ** 2, "near_engine": plan.near_engine(),
             "matvec_ms": statistics.mean(times), "phase_ms_isolated": {k: v[0] for k, v in iso.items()},

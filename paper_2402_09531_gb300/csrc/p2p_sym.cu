@@ -10,11 +10,12 @@
 // kernel constant folded in): the CUDA cores evaluate E' = 2^(2 x'.s'), the
 // point factors sit on the charges and on the finished sums.
 //
-// Arithmetic.  E' is split into FP16 hi + lo (hi = E' truncated to the FP16
-// significand, lo = the FP16 rounding of E' - hi); the charges q' = q * factor, normalised per
+// Arithmetic.  E' is split into FP16 hi + lo (hi = E' rounded to FP16,
+// lo = (E' - hi) * 2^11 rounded to FP16, so that lo stays in FP16's normal
+// range for small E'); the charges q' = q * factor, normalised per
 // right-hand side by a power of two so that |q'| <= 1, are split the same
-// way.  tcgen05.mma.kind::f16 (FP32 accumulation) forms hi*hi + hi*lo +
-// lo*hi, 11-bit significands on both sides like the TF32 split.  The
+// way.  tcgen05.mma.kind::f16 (FP32 accumulation) forms hi*hi in its own
+// columns and hi*lo + lo*hi in others, scaled back by 2^-11 when read.  The
 // plan takes this path only where E' stays inside the FP16 range (E' <=
 // 2^15: the bound on |x'|^2 of the tree's root box) and E' <= 1 otherwise.
 //
@@ -103,17 +104,19 @@ __device__ __forceinline__ float phi_sym(float a) {
   return fmaf(r, e, e);
 }
 
-// Two values -> packed FP16 hi and lo.  hi keeps the top 10 stored mantissa
-// bits of each value (exactly an FP16 number inside its normal range, where
-// E' stays), lo = value - hi is exact in FP32 and rounded to FP16 once: the
-// pair carries ~2^-22 relative.
+// Two values -> packed FP16 hi and lo: hi = the value rounded to FP16, lo =
+// (value - hi) * 2^11 rounded to FP16 (the remainder is exact in FP32; the
+// factor 2^11 keeps lo inside FP16's normal range for values down to
+// ~2^-14, where an unscaled remainder would be subnormal and lose its bits).
+// The pair carries ~2^-23 relative; every product with one lo factor is
+// scaled back by 2^-11 when it is read from TMEM.
+constexpr float kLoScale = 2048.0f, kLoInv = 1.0f / 2048.0f;
 __device__ __forceinline__ void split_f16x2(float e0, float e1, uint32_t& hi, uint32_t& lo) {
-  const float h0 = __uint_as_float(__float_as_uint(e0) & 0xFFFFE000u);
-  const float h1 = __uint_as_float(__float_as_uint(e1) & 0xFFFFE000u);
+  const __half2 h = __floats2half2_rn(e0, e1);
+  const float2 hf = __half22float2(h);
   float l0, l1;
-  up(sub2(pk(e0, e1), pk(h0, h1)), l0, l1);
-  const __half2 h = __floats2half2_rn(h0, h1);
-  const __half2 l = __floats2half2_rn(l0, l1);
+  up(sub2(pk(e0, e1), pk(hf.x, hf.y)), l0, l1);
+  const __half2 l = __floats2half2_rn(l0 * kLoScale, l1 * kLoScale);
   hi = *reinterpret_cast<const uint32_t*>(&h);
   lo = *reinterpret_cast<const uint32_t*>(&l);
 }
@@ -428,7 +431,7 @@ __global__ void __launch_bounds__(kSymThreads, 1) k_near_sym_tc(SymArgs a) {
         for (int r = 0; r < 8; ++r) {
           float* pa = ksum + (ftile * 16 + fr0 + r) * 128 + ta;
           const float acc = pa[0], comp = pa[NT * 16 * 128];
-          const float y = (__uint_as_float(dv[r]) + __uint_as_float(dl[r])) - comp;
+          const float y = (__uint_as_float(dv[r]) + __uint_as_float(dl[r]) * kLoInv) - comp;
           const float s = acc + y;
           pa[NT * 16 * 128] = (s - acc) - y;
           pa[0] = s;
@@ -457,7 +460,8 @@ __global__ void __launch_bounds__(kSymThreads, 1) k_near_sym_tc(SymArgs a) {
         // rows 64..127: E_lo of source 32 (qd - 2) + lane
         const int s = (qd - 2) * 32 + lane;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) cb[(r0 + j) * 64 + s] = __uint_as_float(x[j]) + __uint_as_float(y[j]);
+        for (int j = 0; j < 4; ++j)
+          cb[(r0 + j) * 64 + s] = (__uint_as_float(x[j]) + __uint_as_float(y[j]) * kLoInv) * kLoInv;
         fence_before();
         __syncwarp();
         if (lane == 0) {
@@ -476,7 +480,7 @@ __global__ void __launch_bounds__(kSymThreads, 1) k_near_sym_tc(SymArgs a) {
         unsigned long long* dst = a.acc + (static_cast<int64_t>(S) * 16 + r0) * ld + c * kChunk + s;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          const float v = (__uint_as_float(x[j]) + __uint_as_float(y[j])) + cb[(r0 + j) * 64 + s];
+          const float v = (__uint_as_float(x[j]) + __uint_as_float(y[j]) * kLoInv) + cb[(r0 + j) * 64 + s];
           red_add_u64(dst + static_cast<int64_t>(j) * ld, __float2ll_rn(v * a.acc_scale));
         }
         fence_before();
@@ -601,7 +605,7 @@ __global__ void k_sym_make_bq(const float* xb, const float* pts, int64_t gstride
     v = xb[(g * 16 + r) * ld + s] * f * sc;
   }
   const __half h = __float2half_rn(v);
-  const __half l = __float2half_rn(v - __half2float(h));
+  const __half l = __float2half_rn((v - __half2float(h)) * kLoScale);
   uint16_t* blk = bq + g * static_cast<int64_t>(ld) * 32;
   const int64_t base = (s / 8) * 256 + (s % 8);               // in 2-byte units
   blk[base + (r / 8) * 64 + (r % 8) * 8] = __half_as_ushort(h);
@@ -898,7 +902,7 @@ __global__ void __launch_bounds__(kSymThreads, 1) k_near_sym_gtc(SymGArgs a) {
       tmem_ld8x2(col, col + 16, dv, dl);
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
-        const float y = (__uint_as_float(dv[r]) + __uint_as_float(dl[r])) - kc[r];
+        const float y = (__uint_as_float(dv[r]) + __uint_as_float(dl[r]) * kLoInv) - kc[r];
         const float s = ks[r] + y;
         kc[r] = (s - ks[r]) - y;
         ks[r] = s;
@@ -923,7 +927,8 @@ __global__ void __launch_bounds__(kSymThreads, 1) k_near_sym_gtc(SymGArgs a) {
       if (qd >= 2) {
         const int s = (qd - 2) * 32 + lane;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) cb[(r0 + j) * 64 + s] = __uint_as_float(x[j]) + __uint_as_float(y[j]);
+        for (int j = 0; j < 4; ++j)
+          cb[(r0 + j) * 64 + s] = (__uint_as_float(x[j]) + __uint_as_float(y[j]) * kLoInv) * kLoInv;
         fence_before();
         __syncwarp();
         if (lane == 0) {
@@ -942,7 +947,7 @@ __global__ void __launch_bounds__(kSymThreads, 1) k_near_sym_gtc(SymGArgs a) {
         unsigned long long* dst = a.acc + (static_cast<int64_t>(S) * 16 + r0) * ld + c * kChunk + s;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          const float v = (__uint_as_float(x[j]) + __uint_as_float(y[j])) + cb[(r0 + j) * 64 + s];
+          const float v = (__uint_as_float(x[j]) + __uint_as_float(y[j]) * kLoInv) + cb[(r0 + j) * 64 + s];
           red_add_u64(dst + static_cast<int64_t>(j) * ld, __float2ll_rn(v * a.acc_scale));
         }
         fence_before();
