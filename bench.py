@@ -295,7 +295,7 @@ def phase_rooflines(iso_ms: dict, N: int, R: int, d: int, n: int, n_far: int, de
       l2l_l2p  the same count for the downward pass and the evaluation at the
                sites, FP32 peak
       (far engine "mixed_fp16_tensor": p2m_m2m and l2l_l2p run as FP16 hi/lo
-      contractions on the tensor cores, three products per term: 3x those
+      contractions on the tensor cores, four products per term: 4x those
       flops against the dense FP16 tensor peak, the measured bf16 figure,
       the same nominal rate)
       gather   N R (8 + 4) bytes (float64 in, float32 leaf blocks out), HBM peak
@@ -313,7 +313,7 @@ def phase_rooflines(iso_ms: dict, N: int, R: int, d: int, n: int, n_far: int, de
     if tensor:
         for k in ("p2m_m2m", "l2l_l2p"):
             amount = work[k][0]
-            work[k] = (3 * amount, "tensor flop", tensor_peak, "TFLOP/s")
+            work[k] = (4 * amount, "tensor flop", tensor_peak, "TFLOP/s")
     out = {}
     for k, (amount, kind, peak, unit) in work.items():
         ms = iso_ms.get(k)
@@ -326,7 +326,7 @@ def phase_rooflines(iso_ms: dict, N: int, R: int, d: int, n: int, n_far: int, de
     if tensor:
         for k in ("p2m_m2m", "l2l_l2p"):
             if k in out:
-                out[k]["engine"] = "tcgen05 kind::f16, FP16 hi/lo, 3 products; one or two launches per tree level"
+                out[k]["engine"] = "tcgen05 kind::f16, FP16 hi/lo, 4 products; two launches per tree level"
     return out
 
 

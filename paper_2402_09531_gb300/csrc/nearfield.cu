@@ -236,40 +236,58 @@ void p2p_impl(Plan& P, int Rc, const T* pts, const T* xb, T* ynear, cudaStream_t
 constexpr int kSymMaxRc = 4;
 
 // Per row T of the near list: entries with S >= T (upper) and S < T (lower).
+// One warp per leaf t: the counts of its upper (s >= t) and lower entries.
 __global__ void k_sym_count(const int32_t* rowptr, const int32_t* col, int L, int* nup, int* nlo) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = static_cast<int>((static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
   if (t >= L) return;
   int u = 0, l = 0;
-  for (int e = rowptr[t]; e < rowptr[t + 1]; ++e) (col[e] >= t ? u : l) += 1;
-  nup[t] = u;
-  nlo[t] = l;
+  for (int e = rowptr[t] + lane; e < rowptr[t + 1]; e += 32) (col[e] >= t ? u : l) += 1;
+  for (int o = 16; o > 0; o >>= 1) {
+    u += __shfl_xor_sync(0xffffffffu, u, o);
+    l += __shfl_xor_sync(0xffffffffu, l, o);
+  }
+  if (lane == 0) {
+    nup[t] = u;
+    nlo[t] = l;
+  }
 }
 
+// One warp per leaf t: its upper and lower entries in list order (a ballot
+// per 32 entries keeps the order, so every upper row stays sorted by source).
 __global__ void k_sym_fill(const int32_t* rowptr, const int32_t* col, int L, const int32_t* uprow,
                            const int32_t* lorow, int32_t* up_t, int32_t* up_s, int32_t* lo_src) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = static_cast<int>((static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
   if (t >= L) return;
+  const unsigned below = (1u << lane) - 1u;
   int u = uprow[t], l = lorow[t];
-  for (int e = rowptr[t]; e < rowptr[t + 1]; ++e) {
-    const int s = col[e];
-    if (s >= t) {
-      up_t[u] = t;
-      up_s[u] = s;
-      ++u;
-    } else {
-      lo_src[l++] = s;
+  const int end = rowptr[t + 1];
+  for (int e0 = rowptr[t]; e0 < end; e0 += 32) {
+    const int e = e0 + lane;
+    const int s = e < end ? col[e] : -1;
+    const bool isup = e < end && s >= t, islo = e < end && s < t;
+    const unsigned mu = __ballot_sync(0xffffffffu, isup), ml = __ballot_sync(0xffffffffu, islo);
+    if (isup) {
+      up_t[u + __popc(mu & below)] = t;
+      up_s[u + __popc(mu & below)] = s;
     }
+    if (islo) lo_src[l + __popc(ml & below)] = s;
+    u += __popc(mu);
+    l += __popc(ml);
   }
 }
 
 // Slot of the lower entry (X, T < X): the position of (T, X) in the upper
 // list (each upper row is sorted by source, so a binary search finds it); a
-// missing one means the near relation is not symmetric.
+// missing one means the near relation is not symmetric.  One warp per leaf
+// X, its lanes over X's lower entries.
 __global__ void k_sym_slots(const int32_t* lorow, const int32_t* lo_src, const int32_t* uprow, const int32_t* up_s,
                             int L, int32_t* lo_slot, int* bad) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int x = static_cast<int>((static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
   if (x >= L) return;
-  for (int k = lorow[x]; k < lorow[x + 1]; ++k) {
+  for (int k = lorow[x] + lane; k < lorow[x + 1]; k += 32) {
     const int t = lo_src[k];
     int a = uprow[t], b = uprow[t + 1];   // first entry with up_s >= x in [a, b)
     while (a < b) {
@@ -441,7 +459,8 @@ void build_sym_lists(Plan& P) {
   cl.alloc(L);
   bad.alloc(1);
   DW_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), s));
-  k_sym_count<<<ceil_div(L, 128), 128, 0, s>>>(P.d_near_rowptr.p, P.d_near_col.p, L, cu.p, cl.p);
+  const int warps_grid = ceil_div(static_cast<int64_t>(L) * 32, 128);   // one warp per leaf
+  k_sym_count<<<warps_grid, 128, 0, s>>>(P.d_near_rowptr.p, P.d_near_col.p, L, cu.p, cl.p);
   std::vector<int> hu(L), hl(L);
   DW_CUDA(cudaMemcpyAsync(hu.data(), cu.p, sizeof(int) * L, cudaMemcpyDeviceToHost, s));
   DW_CUDA(cudaMemcpyAsync(hl.data(), cl.p, sizeof(int) * L, cudaMemcpyDeviceToHost, s));
@@ -463,10 +482,10 @@ void build_sym_lists(Plan& P) {
   lo_src.alloc(static_cast<size_t>(std::max<int64_t>(nlo, 1)));
   DW_CUDA(cudaMemcpyAsync(P.sym_uprow.p, up.data(), sizeof(int32_t) * (L + 1), cudaMemcpyHostToDevice, s));
   DW_CUDA(cudaMemcpyAsync(P.sym_lorow.p, lo.data(), sizeof(int32_t) * (L + 1), cudaMemcpyHostToDevice, s));
-  k_sym_fill<<<ceil_div(L, 128), 128, 0, s>>>(P.d_near_rowptr.p, P.d_near_col.p, L, P.sym_uprow.p, P.sym_lorow.p,
-                                             P.sym_t.p, P.sym_s.p, lo_src.p);
-  k_sym_slots<<<ceil_div(L, 128), 128, 0, s>>>(P.sym_lorow.p, lo_src.p, P.sym_uprow.p, P.sym_s.p, L, P.sym_loslot.p,
-                                              bad.p);
+  k_sym_fill<<<warps_grid, 128, 0, s>>>(P.d_near_rowptr.p, P.d_near_col.p, L, P.sym_uprow.p, P.sym_lorow.p,
+                                        P.sym_t.p, P.sym_s.p, lo_src.p);
+  k_sym_slots<<<warps_grid, 128, 0, s>>>(P.sym_lorow.p, lo_src.p, P.sym_uprow.p, P.sym_s.p, L, P.sym_loslot.p,
+                                         bad.p);
   int hbad = 0;
   DW_CUDA(cudaMemcpyAsync(&hbad, bad.p, sizeof(int), cudaMemcpyDeviceToHost, s));
   DW_CUDA(cudaStreamSynchronize(s));

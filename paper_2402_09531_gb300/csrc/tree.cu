@@ -392,10 +392,15 @@ __global__ void k_expand(const int32_t* ct, const int32_t* cs, int64_t nc, const
   }
 }
 
+// Pairs per row; the pairs are sorted by row, so the lanes of a warp that
+// share a row add their count with one atomic.
 __global__ void k_count_rows(const int32_t* pairs, int64_t np, int offset, int* cnt) {
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const unsigned act = __ballot_sync(0xffffffffu, i < np);
   if (i >= np) return;
-  atomicAdd(&cnt[pairs[2 * i] - offset], 1);
+  const int row = pairs[2 * i] - offset;
+  const unsigned same = __match_any_sync(act, row);
+  if ((threadIdx.x & 31) == __ffs(same) - 1) atomicAdd(&cnt[row], __popc(same));
 }
 
 __global__ void k_pair_cols(const int32_t* pairs, int64_t np, int offset, int32_t* col) {
