@@ -66,6 +66,7 @@ using namespace tc;
 
 constexpr int kSymCompWarps = 16;
 constexpr int kSymThreads = (kSymCompWarps + 2) * 32;
+constexpr int kSymGThreads = (kSymCompWarps + 3) * 32;   // two MMA-issuing warps
 constexpr int kChunk = 64;          // sources per chunk
 constexpr int kStages = 4;          // TMA stages (coordinates + FP16 charges of one chunk)
 constexpr int kTmemCols = 256;      // forward 2 entries x 2 tiles x 32, transposed 2 x 32
@@ -690,7 +691,7 @@ struct SymGArgs {
   int* err;
 };
 
-__global__ void __launch_bounds__(kSymThreads, 1) k_near_sym_gtc(SymGArgs a) {
+__global__ void __launch_bounds__(kSymGThreads, 1) k_near_sym_gtc(SymGArgs a) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t bars[32];
   __shared__ uint32_t tmem_slot;
@@ -706,8 +707,8 @@ __global__ void __launch_bounds__(kSymThreads, 1) k_near_sym_gtc(SymGArgs a) {
   uint64_t* gfull = fempty + 2;             // [2] G of a chunk complete
   uint64_t* gfree = gfull + 2;              // [2] G read by the compute warps (16 warps)
   uint64_t* qfull = gfree + 2;              // q_T and 2x'_T landed
-  uint64_t* fin = qfull + 1;
-  static_assert(2 * kStages + 20 <= 32, "barrier array");
+  uint64_t* fin = qfull + 1;                // [2] all MMAs of an issuer complete
+  static_assert(2 * kStages + 21 <= 32, "barrier array");
 
   const int ld = a.ld;              // 256: two 128-target tiles, four 64-source chunks
   constexpr int NT = 2, NC = 4;
@@ -723,26 +724,30 @@ __global__ void __launch_bounds__(kSymThreads, 1) k_near_sym_gtc(SymGArgs a) {
   unsigned char* qT = stages + kStages * stage_bytes;               // 16 KB
   unsigned char* xT = qT + ld * 64;                                  // 16 KB
   float* comb = reinterpret_cast<float*>(xT + kXBytesLeaf256);      // [2][16][64]
-  constexpr uint32_t kG = 0, kF = 256, kTr = 384;                    // TMEM column bases
+  // TMEM column bases: G, forward accumulators, transposed accumulators of
+  // the two issuers (target tile 0 and 1: the two K halves of E^T q_T)
+  constexpr uint32_t kG = 0, kF = 256, kTr = 384, kTr1 = 448;
 
   if (t == 0) {
+    // barriers the MMAs complete count one commit of each of the two issuers
     for (int i = 0; i < kStages; ++i) {
       bar_init(&full[i], 1);
-      bar_init(&sfree[i], 1);
+      bar_init(&sfree[i], 2);
     }
     for (int i = 0; i < 2; ++i) {
       bar_init(&efull[i], kSymCompWarps);
-      bar_init(&efree[i], 1);
-      bar_init(&tfull[i], 1);
+      bar_init(&efree[i], 2);
+      bar_init(&tfull[i], 2);
       bar_init(&tempty[i], kSymCompWarps);
       bar_init(&cready[i], kSymCompWarps / 2);
-      bar_init(&ffull[i], 1);
+      bar_init(&ffull[i], 2);
       bar_init(&fempty[i], kSymCompWarps);
-      bar_init(&gfull[i], 1);
+      bar_init(&gfull[i], 2);
       bar_init(&gfree[i], kSymCompWarps);
     }
     bar_init(qfull, 1);
-    bar_init(fin, 1);
+    bar_init(&fin[0], 1);
+    bar_init(&fin[1], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) tmem_alloc(&tmem_slot, 512);
@@ -784,8 +789,11 @@ __global__ void __launch_bounds__(kSymThreads, 1) k_near_sym_gtc(SymGArgs a) {
         (void)wait_sleep(&full[j % kStages], static_cast<uint32_t>((j / kStages) & 1));
       if (bad) atomicExch(a.err, 3);
     }
-  } else if (warp == kSymCompWarps) {
-    // ---- MMA issuer: G of chunk i + 2 ahead of the products of chunk i
+  } else if (warp == kSymCompWarps || warp == kSymCompWarps + 2) {
+    // ---- MMA issuers, one per target tile (the MMAs of two issuing threads
+    // proceed concurrently; one thread's issue rate bounds the kernel
+    // otherwise): G of chunk i + 2 ahead of the products of chunk i
+    const int at = warp == kSymCompWarps ? 0 : 1;
     if (lane == 0) {
       bool bad = !wait_sleep(qfull, 0u);
       const uint32_t ebase = sptr(ebuf), sbase = sptr(stages), qtb = sptr(qT), xtb = sptr(xT);
@@ -805,8 +813,7 @@ __global__ void __launch_bounds__(kSymThreads, 1) k_near_sym_gtc(SymGArgs a) {
         if (i >= 2 && !wait_sleep(&gfree[gb], static_cast<uint32_t>(((i - 2) >> 1) & 1))) return false;
         fence_after();
         const u64 bhi = dG_b + ((st * stage_bytes) >> 4), blo = bhi + (kXChunkHalf >> 4);
-#pragma unroll
-        for (int at = 0; at < NT; ++at) {
+        {
           const u64 ahi = dG_a + ((at * 16 * 256) >> 4), alo = ahi + (xlo >> 4);
           const uint32_t d = tmem + kG + static_cast<uint32_t>(gb * 128 + at * 64);
           mma_f16(d, ahi, blo, kIdG, 0u);                // small terms first,
@@ -841,8 +848,7 @@ __global__ void __launch_bounds__(kSymThreads, 1) k_near_sym_gtc(SymGArgs a) {
           fence_after();
           const u64 fa = dF_a + ((eb * ebytes) >> 4);
           const u64 fb_desc = dF_b + ((st * stage_bytes) >> 4);
-#pragma unroll
-          for (int at = 0; at < NT; ++at) {
+          {
             const uint32_t dcol = tmem + kF + static_cast<uint32_t>(fb * 64 + at * 32);
 #pragma unroll
             for (int kk = 0; kk < kChunk / 16; ++kk) {
@@ -859,11 +865,14 @@ __global__ void __launch_bounds__(kSymThreads, 1) k_near_sym_gtc(SymGArgs a) {
               break;
             }
             fence_after();
-            const uint32_t dcol = tmem + kTr + static_cast<uint32_t>(tb * 32);
+            // this issuer's K half: the targets of its tile
+            const uint32_t dcol = tmem + (at == 0 ? kTr : kTr1) + static_cast<uint32_t>(tb * 32);
             const u64 ta = dT_a + ((eb * ebytes) >> 4);
 #pragma unroll
-            for (int j = 0; j < NT * 8; ++j)
-              mma_f16(dcol, ta + ((j * 2 * kTS) >> 4), dT_b + ((j * 2 * 512) >> 4), kIdTrn32, j > 0 ? 1u : 0u);
+            for (int jj = 0; jj < 8; ++jj) {
+              const int j = 8 * at + jj;
+              mma_f16(dcol, ta + ((j * 2 * kTS) >> 4), dT_b + ((j * 2 * 512) >> 4), kIdTrn32, jj > 0 ? 1u : 0u);
+            }
             mma_commit(&tfull[tb]);
             ++jt;
           }
@@ -872,8 +881,8 @@ __global__ void __launch_bounds__(kSymThreads, 1) k_near_sym_gtc(SymGArgs a) {
           if (c == NC - 1) mma_commit(&ffull[fb]);
         }
       }
-      mma_commit(fin);
-      (void)wait_sleep(fin, 0u);
+      mma_commit(&fin[at]);
+      (void)wait_sleep(&fin[at], 0u);
       if (bad) atomicExch(a.err, 3);
     }
   } else {
@@ -921,8 +930,14 @@ __global__ void __launch_bounds__(kSymThreads, 1) k_near_sym_gtc(SymGArgs a) {
       fence_after();
       const int r0 = 4 * part;
       const uint32_t col = lane_base + kTr + static_cast<uint32_t>(tb * 32 + r0);
-      uint32_t x[4], y[4];
+      uint32_t x[4], y[4], x1[4], y1[4];
       tmem_ld4x2(col, col + 16, x, y);
+      tmem_ld4x2(col + (kTr1 - kTr), col + (kTr1 - kTr) + 16, x1, y1);   // the other K half
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        x[j] = __float_as_uint(__uint_as_float(x[j]) + __uint_as_float(x1[j]));
+        y[j] = __float_as_uint(__uint_as_float(y[j]) + __uint_as_float(y1[j]));
+      }
       float* cb = comb + tb * (64 * 16);
       if (qd >= 2) {
         const int s = (qd - 2) * 32 + lane;
@@ -1165,7 +1180,7 @@ bool near_sym_tc(Plan& P, int D, int Rc, cudaStream_t s) {
     g.acc_scale = std::ldexp(1.0f, sb);
     g.ld = ld;
     g.err = P.d_err.p;
-    k_near_sym_gtc<<<P.L, kSymThreads, sym_g_smem(), s>>>(g);
+    k_near_sym_gtc<<<P.L, kSymGThreads, sym_g_smem(), s>>>(g);
     DW_CUDA(cudaGetLastError());
     k_sym_finish<<<ceil_div(nsite, 256), 256, 0, s>>>(P.sym_fwd.p, P.sym_acc.p, std::ldexp(1.0, -sb), P.d_ptsk.p,
                                                        gstride, P.L, ld, D, gauss, Rc, P.sym_colmax.p, P.ynear32.p,
