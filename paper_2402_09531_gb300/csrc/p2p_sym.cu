@@ -66,7 +66,7 @@ using namespace tc;
 
 constexpr int kSymCompWarps = 16;
 constexpr int kSymThreads = (kSymCompWarps + 2) * 32;
-constexpr int kSymGThreads = (kSymCompWarps + 3) * 32;   // two MMA-issuing warps
+constexpr int kSymGThreads = (kSymCompWarps + 5) * 32;   // four MMA-issuing warps
 constexpr int kChunk = 64;          // sources per chunk
 constexpr int kStages = 4;          // TMA stages (coordinates + FP16 charges of one chunk)
 constexpr int kTmemCols = 256;      // forward 2 entries x 2 tiles x 32, transposed 2 x 32
@@ -707,8 +707,8 @@ __global__ void __launch_bounds__(kSymGThreads, 1) k_near_sym_gtc(SymGArgs a) {
   uint64_t* gfull = fempty + 2;             // [2] G of a chunk complete
   uint64_t* gfree = gfull + 2;              // [2] G read by the compute warps (16 warps)
   uint64_t* qfull = gfree + 2;              // q_T and 2x'_T landed
-  uint64_t* fin = qfull + 1;                // [2] all MMAs of an issuer complete
-  static_assert(2 * kStages + 21 <= 32, "barrier array");
+  uint64_t* fin = qfull + 1;                // [4] all MMAs of an issuer complete
+  static_assert(2 * kStages + 23 <= 32, "barrier array");
 
   const int ld = a.ld;              // 256: two 128-target tiles, four 64-source chunks
   constexpr int NT = 2, NC = 4;
@@ -729,14 +729,16 @@ __global__ void __launch_bounds__(kSymGThreads, 1) k_near_sym_gtc(SymGArgs a) {
   constexpr uint32_t kG = 0, kF = 256, kTr = 384, kTr1 = 448;
 
   if (t == 0) {
-    // barriers the MMAs complete count one commit of each of the two issuers
+    // barriers the MMAs complete count one commit of each issuer that uses
+    // the resource: the stage and G (two G/forward issuers), the E tile (all
+    // four), the transposed accumulators (two transposed issuers)
     for (int i = 0; i < kStages; ++i) {
       bar_init(&full[i], 1);
       bar_init(&sfree[i], 2);
     }
     for (int i = 0; i < 2; ++i) {
       bar_init(&efull[i], kSymCompWarps);
-      bar_init(&efree[i], 2);
+      bar_init(&efree[i], 4);
       bar_init(&tfull[i], 2);
       bar_init(&tempty[i], kSymCompWarps);
       bar_init(&cready[i], kSymCompWarps / 2);
@@ -746,8 +748,7 @@ __global__ void __launch_bounds__(kSymGThreads, 1) k_near_sym_gtc(SymGArgs a) {
       bar_init(&gfree[i], kSymCompWarps);
     }
     bar_init(qfull, 1);
-    bar_init(&fin[0], 1);
-    bar_init(&fin[1], 1);
+    for (int i = 0; i < 4; ++i) bar_init(&fin[i], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) tmem_alloc(&tmem_slot, 512);
@@ -789,14 +790,55 @@ __global__ void __launch_bounds__(kSymGThreads, 1) k_near_sym_gtc(SymGArgs a) {
         (void)wait_sleep(&full[j % kStages], static_cast<uint32_t>((j / kStages) & 1));
       if (bad) atomicExch(a.err, 3);
     }
+  } else if (warp >= kSymCompWarps + 3) {
+    // ---- transposed-product issuers, one per target tile (its K half of
+    // E^T q_T), beside the G / forward issuers: MMAs issued by several
+    // threads proceed concurrently, one thread's issue rate bounded the kernel
+    const int at = warp - (kSymCompWarps + 3);
+    if (lane == 0) {
+      bool bad = !wait_sleep(qfull, 0u);
+      const u64 dT_a = smem_desc(sptr(ebuf), kSymTrnLbo, kSymTrnSbo);   // E tile 0, transposed A
+      const u64 dT_b = smem_desc(sptr(qT), 512, 128);                     // q_T
+      int i = 0, jt = 0;
+      for (int e = 0; e < ne && !bad; ++e) {
+        const bool diag = a.ups[e0 + e] == T;
+        for (int c = 0; c < NC; ++c, ++i) {
+          const int eb = i & 1;
+          if (!wait_sleep(&efull[eb], static_cast<uint32_t>((i >> 1) & 1))) {
+            bad = true;
+            break;
+          }
+          if (!diag) {
+            const int tb = jt & 1;
+            if (jt >= 2 && !wait_sleep(&tempty[tb], static_cast<uint32_t>(((jt - 2) >> 1) & 1))) {
+              bad = true;
+              break;
+            }
+            fence_after();
+            const uint32_t dcol = tmem + (at == 0 ? kTr : kTr1) + static_cast<uint32_t>(tb * 32);
+            const u64 ta = dT_a + ((eb * ebytes) >> 4);
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) {
+              const int j = 8 * at + jj;
+              mma_f16(dcol, ta + ((j * 2 * kTS) >> 4), dT_b + ((j * 2 * 512) >> 4), kIdTrn32, jj > 0 ? 1u : 0u);
+            }
+            mma_commit(&tfull[tb]);
+            ++jt;
+          }
+          mma_commit(&efree[eb]);
+        }
+      }
+      mma_commit(&fin[2 + at]);
+      (void)wait_sleep(&fin[2 + at], 0u);
+      if (bad) atomicExch(a.err, 3);
+    }
   } else if (warp == kSymCompWarps || warp == kSymCompWarps + 2) {
-    // ---- MMA issuers, one per target tile (the MMAs of two issuing threads
-    // proceed concurrently; one thread's issue rate bounds the kernel
-    // otherwise): G of chunk i + 2 ahead of the products of chunk i
+    // ---- G / forward issuers, one per target tile: G of chunk i + 2 ahead
+    // of the forward products of chunk i
     const int at = warp == kSymCompWarps ? 0 : 1;
     if (lane == 0) {
       bool bad = !wait_sleep(qfull, 0u);
-      const uint32_t ebase = sptr(ebuf), sbase = sptr(stages), qtb = sptr(qT), xtb = sptr(xT);
+      const uint32_t ebase = sptr(ebuf), sbase = sptr(stages), xtb = sptr(xT);
       constexpr uint32_t xlo = 256 * kKD * 2;            // hi -> lo in the target block (bytes)
       // G MMAs of chunk i (stage i % kStages) into G buffer i & 1
       // descriptors: the start address is the low field (address / 16), so a
@@ -805,8 +847,6 @@ __global__ void __launch_bounds__(kSymGThreads, 1) k_near_sym_gtc(SymGArgs a) {
       const u64 dG_a = smem_desc(xtb, 128, 256);                    // target tile 0 (hi)
       const u64 dF_a = smem_desc(ebase, 128, kTS);                  // E tile 0, forward A (hi)
       const u64 dF_b = smem_desc(sbase + 2 * kXChunkHalf, 512, 128);   // stage 0 charges
-      const u64 dT_a = smem_desc(ebase, kSymTrnLbo, kSymTrnSbo);    // E tile 0, transposed A
-      const u64 dT_b = smem_desc(qtb, 512, 128);                     // q_T
       auto issue_g = [&](int i) -> bool {
         const int st = i % kStages, gb = i & 1;
         if (!wait_sleep(&full[st], static_cast<uint32_t>((i / kStages) & 1))) return false;
@@ -826,13 +866,10 @@ __global__ void __launch_bounds__(kSymGThreads, 1) k_near_sym_gtc(SymGArgs a) {
       // G runs two chunks ahead of the products: G(i + 2) goes into the
       // buffer of G(i) as soon as the compute warps have read G(i), so the
       // products never wait on a G still queued behind other MMAs
-      int jt = 0;
       if (nchunks > 0 && !bad) bad = !issue_g(0);
       if (nchunks > 1 && !bad) bad = !issue_g(1);
       int i = 0;
       for (int e = 0; e < ne && !bad; ++e) {
-        const int S = a.ups[e0 + e];
-        const bool diag = S == T;
         const int fb = e & 1;
         for (int c = 0; c < NC; ++c, ++i) {
           if (i + 2 < nchunks && !issue_g(i + 2)) {
@@ -857,24 +894,6 @@ __global__ void __launch_bounds__(kSymGThreads, 1) k_near_sym_gtc(SymGArgs a) {
               mma_f16(dcol, ahi, bq, kIdFwd32, (c > 0 || kk > 0) ? 1u : 0u);
               mma_f16(dcol + 16, ahi + (kHL >> 4), bq, kIdFwd16, 1u);
             }
-          }
-          if (!diag) {
-            const int tb = jt & 1;
-            if (jt >= 2 && !wait_sleep(&tempty[tb], static_cast<uint32_t>(((jt - 2) >> 1) & 1))) {
-              bad = true;
-              break;
-            }
-            fence_after();
-            // this issuer's K half: the targets of its tile
-            const uint32_t dcol = tmem + (at == 0 ? kTr : kTr1) + static_cast<uint32_t>(tb * 32);
-            const u64 ta = dT_a + ((eb * ebytes) >> 4);
-#pragma unroll
-            for (int jj = 0; jj < 8; ++jj) {
-              const int j = 8 * at + jj;
-              mma_f16(dcol, ta + ((j * 2 * kTS) >> 4), dT_b + ((j * 2 * 512) >> 4), kIdTrn32, jj > 0 ? 1u : 0u);
-            }
-            mma_commit(&tfull[tb]);
-            ++jt;
           }
           mma_commit(&efree[eb]);
           mma_commit(&sfree[st]);
