@@ -556,6 +556,8 @@ def run_ours(args):
                                        f"(derived: no measured FP32 peak)"},
             "phase_ms_isolated": {k: v[0] / 2 for k, v in iso.items()},
             "far_engine": plan.far_engine(),
+            "m2l_engine": plan.m2l_engine(), "m2l_tune_ms": {"symmetric": plan.m2l_tune_ms()[0],
+                                                              "ordered": plan.m2l_tune_ms()[1]},
             "phase_roofline": phase_rooflines({k: v[0] / 2 for k, v in iso.items()}, N, R, d, n_x, n_far, depth,
                                               acct["evals"], peak, float(peaks.get("hbm_gbs", 6804.8)),
                                               plan.far_engine(), float(peaks.get("bf16_tflops", 1900.0))),

@@ -335,6 +335,32 @@ dwfmm_status dwfmm_near_engine(dwfmm_plan plan, int32_t* engine);
  * most 20 nonzero entries; otherwise engine 1.  Errors: INVALID_ARG. */
 dwfmm_status dwfmm_far_engine(dwfmm_plan plan, int32_t* engine);
 
+/* Which engine ran the couplings (M2L, Eq. (5.4): the far blocks S_{t,s}
+ * applied to the node charges) in the plan's last matvec (*engine, -1 before
+ * the first): 0 float64 CUDA cores; 1 float32 CUDA cores; 2 MIXED, every
+ * ordered far pair, contraction on the tensor cores (TF32 hi/lo); 3 MIXED,
+ * each unordered far pair (t, s > t) once on the symmetric tensor-core
+ * engine of the near field (FP16 hi/lo, fixed-point transposed sums, node
+ * sets padded to 128 slots).  For MIXED plans with 9..16 right-hand sides
+ * the engine is the caller's choice (dwfmm_plan_set_m2l_engine) or, by
+ * default, the faster of 2 and 3 as timed once per tree (engine 3 needs
+ * |Lambda| <= 128 and a symmetric far list).  Errors: INVALID_ARG. */
+dwfmm_status dwfmm_m2l_engine(dwfmm_plan plan, int32_t* engine);
+
+/* Choose the M2L engine of MIXED matvecs with 9..16 right-hand sides:
+ * -1 (the default) times engines 2 and 3 at the first such matvec of each
+ * tree (before its near field starts, on the plan's moment buffer, zeroed)
+ * and keeps the faster; 2 or 3 forces that engine (3 falls back to 2 where
+ * it does not apply).  Both meet the float32 tolerance; engine 3 evaluates
+ * each far pair once and is the more accurate.  Takes effect at the next
+ * matvec.  Errors: INVALID_ARG (another value).  No counterpart in the
+ * paper. */
+dwfmm_status dwfmm_plan_set_m2l_engine(dwfmm_plan plan, int32_t engine);
+
+/* The timing behind the default choice: ms[0] engine 3, ms[1] engine 2 (one
+ * M2L each, -1 where not timed or not applicable).  `ms`: host, 2 doubles. */
+dwfmm_status dwfmm_m2l_tune_ms(dwfmm_plan plan, double* ms);
+
 /* Copy out plan data (host buffers, NULL to skip), for tests and tools:
  *  weights: d doubles; lam: n x d int32 multi-indices (row-major);
  *  nodes: n x d doubles; pivots: n int32 Halton indices (0-based, -1 if the

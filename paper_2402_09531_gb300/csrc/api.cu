@@ -82,6 +82,19 @@ void Plan::free_tree() {
   sym_xa16.release();
   sym_xb16.release();
   sym_x16_ok = false;
+  fsym_uprow.release();
+  fsym_s.release();
+  fsym_order.release();
+  fsym_rows = 0;
+  fsym_ok = false;
+  m2l_crd.release();
+  m2l_crd_D = -1;
+  m2l_bq16.release();
+  m2l_fwd.release();
+  m2l_acc.release();
+  m2l_colmax.release();
+  m2l_tuned = -1;
+  m2l_tune_ms[0] = m2l_tune_ms[1] = -1.0;
   dpad = -1;
 }
 
@@ -289,6 +302,7 @@ dwfmm_status dwfmm_tree_build(dwfmm_plan plan, const double* pts, int64_t n, int
     dw::build_lists(P);
     dw::build_cluster_data(P);
     dw::build_sym_lists(P);
+    if (P.prec == DWFMM_P_MIXED) dw::build_far_sym_lists(P);
     // bound of |x'|^2 = |x|^2 log2(e) / (2 sigma^2) over the root box, which
     // holds every site and every interpolation node
     P.gauss_fact = false;
@@ -424,6 +438,25 @@ dwfmm_status dwfmm_plan_destroy(dwfmm_plan plan) {
 dwfmm_status dwfmm_near_engine(dwfmm_plan plan, int32_t* engine) {
   if (!plan || !engine) return DWFMM_ERR_INVALID_ARG;
   *engine = plan->P.near_engine;
+  return DWFMM_OK;
+}
+
+dwfmm_status dwfmm_m2l_engine(dwfmm_plan plan, int32_t* engine) {
+  if (!plan || !engine) return DWFMM_ERR_INVALID_ARG;
+  *engine = plan->P.m2l_engine;
+  return DWFMM_OK;
+}
+
+dwfmm_status dwfmm_plan_set_m2l_engine(dwfmm_plan plan, int32_t engine) {
+  if (!plan || (engine != -1 && engine != 2 && engine != 3)) return DWFMM_ERR_INVALID_ARG;
+  plan->P.m2l_pref = engine;
+  return DWFMM_OK;
+}
+
+dwfmm_status dwfmm_m2l_tune_ms(dwfmm_plan plan, double* ms) {
+  if (!plan || !ms) return DWFMM_ERR_INVALID_ARG;
+  ms[0] = plan->P.m2l_tune_ms[0];
+  ms[1] = plan->P.m2l_tune_ms[1];
   return DWFMM_OK;
 }
 

@@ -297,6 +297,23 @@ struct Plan {
   DBuf<uint16_t> sym_xa16, sym_xb16;   // FP16 hi/lo coordinate blocks (2x' and x') of the Gaussian path
   bool sym_x16_ok = false;
   int near_engine = -1;   // engine of the last near field (dwfmm_near_engine)
+  // symmetric tensor-core M2L (MIXED): upper entries (t, s > t) of the far
+  // list by target cluster, target clusters by decreasing upper-row length
+  // (the first fsym_rows have entries), node coordinates in 128-slot
+  // blocks, FP16 charge blocks, forward and fixed-point transposed sums
+  DBuf<int32_t> fsym_uprow, fsym_s, fsym_order;
+  int fsym_rows = 0;
+  bool fsym_ok = false;
+  DBuf<float> m2l_crd;
+  int m2l_crd_D = -1;
+  DBuf<uint16_t> m2l_bq16;
+  DBuf<float> m2l_fwd;
+  DBuf<unsigned long long> m2l_acc;
+  DBuf<unsigned> m2l_colmax;
+  int m2l_engine = -1;    // engine of the last M2L (dwfmm_m2l_engine)
+  int m2l_pref = -1;      // engine chosen by the caller (dwfmm_plan_set_m2l_engine), -1 = timed
+  int m2l_tuned = -1;     // engine the timing chose for this tree (-1 = not yet timed)
+  double m2l_tune_ms[2] = {-1.0, -1.0};   // symmetric, ordered
   // tensor-core far field (MIXED): FP16 hi/lo tiles of V^{-T} and V^{-1}
   // scaled by 2^-far_vexp, valid for the current node set
   DBuf<uint16_t> far_vt;
@@ -344,6 +361,9 @@ void launch_nearfield(Plan& P, int Rc, bool fp64, cudaStream_t s);
 uint64_t device_bit();
 void build_sym_lists(Plan& P);              // upper / lower near lists (symmetric float64 P2P)
 void sym_tc_order(Plan& P, const std::vector<int>& upper_counts);
+bool m2l_sym_tc(Plan& P, int D, int Rc, cudaStream_t s);   // p2p_sym.cu
+void m2l_autotune(Plan& P, int Rc);                         // p2p_f32.cu
+void build_far_sym_lists(Plan& P);                          // nearfield.cu
 bool near_sym_tc(Plan& P, int D, int Rc, cudaStream_t s);   // symmetric tensor-core P2P (MIXED, 9..16 RHS)
 int sm_count();
 bool p2p_f32_tuned(Plan& P, int Rc, cudaStream_t s);

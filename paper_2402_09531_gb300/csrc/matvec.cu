@@ -71,6 +71,7 @@ void matvec_device(Plan& P, const double* x, int64_t ldx, double* y, int64_t ldy
     timer_begin(P, 0, s);
     launch_gather(P, x, ldx, r0, Rc, fp64);
     timer_end(P, 0, s, 1);
+    if (!fp64) m2l_autotune(P, Rc);   // once per tree, before the near field starts
     if (P.tm.on && P.tm.serialize) {  // every phase alone on the caller's stream
       launch_farfield(P, Rc, fp64);
       timer_begin(P, 4, s);

@@ -496,6 +496,65 @@ void build_sym_lists(Plan& P) {
   sym_tc_order(P, hu);
 }
 
+// Upper entries (t, s > t) of the far list (Eq. (5.1): admissible pairs of
+// one level, both orderings listed) for the symmetric tensor-core M2L: rows
+// by target cluster, sorted by source like the list; target clusters ordered
+// by decreasing upper-row length, the ones with entries first.  The relation
+// must be symmetric (checked through the slots of the lower entries) and
+// holds no diagonal entry.
+void build_far_sym_lists(Plan& P) {
+  P.fsym_ok = false;
+  P.fsym_rows = 0;
+  const int C = P.C;
+  if (P.N == 0 || C <= 0 || P.nfar <= 0) return;
+  cudaStream_t s = P.stream;
+  DBuf<int> cu, cl, bad;
+  cu.alloc(C);
+  cl.alloc(C);
+  bad.alloc(1);
+  DW_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), s));
+  const int warps_grid = ceil_div(static_cast<int64_t>(C) * 32, 128);   // one warp per cluster
+  k_sym_count<<<warps_grid, 128, 0, s>>>(P.d_far_rowptr.p, P.d_far_col.p, C, cu.p, cl.p);
+  std::vector<int> hu(C), hl(C);
+  DW_CUDA(cudaMemcpyAsync(hu.data(), cu.p, sizeof(int) * C, cudaMemcpyDeviceToHost, s));
+  DW_CUDA(cudaMemcpyAsync(hl.data(), cl.p, sizeof(int) * C, cudaMemcpyDeviceToHost, s));
+  DW_CUDA(cudaStreamSynchronize(s));
+  std::vector<int32_t> up(C + 1, 0), lo(C + 1, 0);
+  for (int t = 0; t < C; ++t) {
+    up[t + 1] = up[t] + hu[t];
+    lo[t + 1] = lo[t] + hl[t];
+  }
+  const int64_t nup = up[C], nlo = lo[C];
+  if (nup != nlo || nup <= 0) return;   // a symmetric relation without diagonal entries
+  P.fsym_uprow.alloc(C + 1);
+  P.fsym_s.alloc(static_cast<size_t>(nup));
+  DBuf<int32_t> lorow, up_t, lo_src, lo_slot;
+  lorow.alloc(C + 1);
+  up_t.alloc(static_cast<size_t>(nup));
+  lo_src.alloc(static_cast<size_t>(nlo));
+  lo_slot.alloc(static_cast<size_t>(nlo));
+  DW_CUDA(cudaMemcpyAsync(P.fsym_uprow.p, up.data(), sizeof(int32_t) * (C + 1), cudaMemcpyHostToDevice, s));
+  DW_CUDA(cudaMemcpyAsync(lorow.p, lo.data(), sizeof(int32_t) * (C + 1), cudaMemcpyHostToDevice, s));
+  k_sym_fill<<<warps_grid, 128, 0, s>>>(P.d_far_rowptr.p, P.d_far_col.p, C, P.fsym_uprow.p, lorow.p, up_t.p,
+                                        P.fsym_s.p, lo_src.p);
+  k_sym_slots<<<warps_grid, 128, 0, s>>>(lorow.p, lo_src.p, P.fsym_uprow.p, P.fsym_s.p, C, lo_slot.p, bad.p);
+  int hbad = 0;
+  DW_CUDA(cudaMemcpyAsync(&hbad, bad.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  DW_CUDA(cudaStreamSynchronize(s));
+  DW_CUDA(cudaGetLastError());
+  if (hbad) return;
+  std::vector<int32_t> ord(C);
+  for (int i = 0; i < C; ++i) ord[i] = i;
+  std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return hu[x] > hu[y]; });
+  int rows = 0;
+  while (rows < C && hu[ord[rows]] > 0) ++rows;
+  P.fsym_order.alloc(C);
+  DW_CUDA(cudaMemcpyAsync(P.fsym_order.p, ord.data(), sizeof(int32_t) * C, cudaMemcpyHostToDevice, s));
+  DW_CUDA(cudaStreamSynchronize(s));
+  P.fsym_rows = rows;
+  P.fsym_ok = true;
+}
+
 // Every target block against every source leaf in float64 (exact evaluation).
 void eval_f64(Plan& P, const double* tgt64, int G, const int32_t* rowptr, const int32_t* col, int Rc, double* out,
               cudaStream_t s) {
@@ -509,8 +568,13 @@ void eval_f64(Plan& P, const double* tgt64, int G, const int32_t* rowptr, const 
 
 void launch_m2l(Plan& P, int Rc, bool fp64) {
   if (P.jmin > P.J) return;
-  if (fp64) m2l_impl<double>(P, Rc, P.d_ynode64.p, P.mom64.p, P.loc64.p);
-  else if (!m2l_f32_tuned(P, Rc)) m2l_impl<float>(P, Rc, P.d_ynode32.p, P.mom32.p, P.loc32.p);
+  if (fp64) {
+    P.m2l_engine = 0;
+    m2l_impl<double>(P, Rc, P.d_ynode64.p, P.mom64.p, P.loc64.p);
+  } else if (!m2l_f32_tuned(P, Rc)) {
+    P.m2l_engine = 1;
+    m2l_impl<float>(P, Rc, P.d_ynode32.p, P.mom32.p, P.loc32.p);
+  }
   DW_CUDA(cudaGetLastError());
 }
 

@@ -576,6 +576,63 @@ void eval_f32(Plan& P, const double* tgt64, int G, const int32_t* rowptr, const 
   DW_CUDA(cudaGetLastError());
 }
 
+namespace {
+
+// The ordered-pair tensor-core M2L (every far block, both orderings):
+// interleaved moments, then the kernel-summation engine on node sets.
+bool m2l_ordered_tc(Plan& P, int D, int Rc) {
+  const int first = (1 << P.jmin) - 1;
+  P.momq32.alloc(static_cast<size_t>(P.C) * P.n_pad * kRC);
+  const int64_t nq = static_cast<int64_t>(P.C) * P.n_pad * 16;
+  k_interleave<<<ceil_div(nq, 256), 256, 0, P.stream>>>(P.mom32.p, P.C, P.n_pad, 16, P.momq32.p);
+  // own charge-block scratch: the near field runs concurrently on the side stream
+  return sum_tc(D, P.kernel, P.d_ynodek.p, static_cast<int64_t>(D + 1) * P.n_pad, P.d_ynodek.p,
+                static_cast<int64_t>(D + 1) * P.n_pad, P.momq32.p, P.C, P.bqm32, P.loc32.p,
+                static_cast<int64_t>(kRC) * P.n_pad, P.d_far_rowptr.p, P.d_far_col.p, nullptr, 0, P.n, first,
+                P.C - first, P.n_pad, Rc, P.gauss_fact, P.d_err.p, P.stream);
+}
+
+}  // namespace
+
+// MIXED plans with 9..16 right-hand sides have two tensor-core M2L engines
+// (every ordered far pair, TF32 hi/lo; each unordered pair once, FP16 hi/lo
+// with fixed-point transposed sums).  Unless the caller chose one, the
+// first such matvec of a tree times both on the plan's moments buffer (set
+// to zero; values do not change the time) before the near field starts,
+// and the faster is kept for the tree.  Not while the stream is being
+// captured or the phase timers run (the ordered engine then).
+void m2l_autotune(Plan& P, int Rc) {
+  if (P.prec != DWFMM_P_MIXED || Rc < 9 || Rc > 16 || P.m2l_pref >= 0 || P.m2l_tuned >= 0) return;
+  if (P.jmin > P.J || P.tm.on) return;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  DW_CUDA(cudaStreamIsCapturing(P.stream, &cs));
+  if (cs != cudaStreamCaptureStatusNone) return;
+  const int D = padded_dim(P.d);
+  if (D < 0 || stage_bytes(D, 16, P.n_pad) > 200 * 1024) return;
+  ensure_attrs();
+  ensure_scaled(P, D);
+  DW_CUDA(cudaMemsetAsync(P.mom32.p, 0, static_cast<size_t>(P.C) * kRC * P.n_pad * sizeof(float), P.stream));
+  cudaEvent_t e0, e1, e2;
+  DW_CUDA(cudaEventCreate(&e0));
+  DW_CUDA(cudaEventCreate(&e1));
+  DW_CUDA(cudaEventCreate(&e2));
+  DW_CUDA(cudaEventRecord(e0, P.stream));
+  const bool sym = m2l_sym_tc(P, D, Rc, P.stream);
+  DW_CUDA(cudaEventRecord(e1, P.stream));
+  const bool ord = m2l_ordered_tc(P, D, Rc);
+  DW_CUDA(cudaEventRecord(e2, P.stream));
+  DW_CUDA(cudaEventSynchronize(e2));
+  float ms_sym = 0.f, ms_ord = 0.f;
+  DW_CUDA(cudaEventElapsedTime(&ms_sym, e0, e1));
+  DW_CUDA(cudaEventElapsedTime(&ms_ord, e1, e2));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaEventDestroy(e2);
+  P.m2l_tune_ms[0] = sym ? ms_sym : -1.0;
+  P.m2l_tune_ms[1] = ord ? ms_ord : -1.0;
+  P.m2l_tuned = (sym && (!ord || ms_sym < ms_ord)) ? 3 : 2;
+}
+
 bool m2l_f32_tuned(Plan& P, int Rc) {
   const int D = padded_dim(P.d);
   if (D < 0) return false;
@@ -584,18 +641,22 @@ bool m2l_f32_tuned(Plan& P, int Rc) {
   if (smem > 200 * 1024) return false;
   ensure_attrs();
   ensure_scaled(P, D);
+  if (P.prec == DWFMM_P_MIXED && RC == 16) {
+    const int want = P.m2l_pref >= 0 ? P.m2l_pref : (P.m2l_tuned >= 0 ? P.m2l_tuned : 2);
+    if (want == 3 && m2l_sym_tc(P, D, Rc, P.stream)) {
+      P.m2l_engine = 3;
+      return true;
+    }
+    if (m2l_ordered_tc(P, D, Rc)) {
+      P.m2l_engine = 2;
+      return true;
+    }
+  }
   const int first = (1 << P.jmin) - 1;
   P.momq32.alloc(static_cast<size_t>(P.C) * P.n_pad * kRC);
   const int64_t nq = static_cast<int64_t>(P.C) * P.n_pad * RC;
   k_interleave<<<ceil_div(nq, 256), 256, 0, P.stream>>>(P.mom32.p, P.C, P.n_pad, RC, P.momq32.p);
-  // MIXED plans with 9..16 right-hand sides: contraction on the tensor cores
-  // (own charge-block scratch: the near field runs concurrently on the side stream)
-  if (P.prec == DWFMM_P_MIXED && RC == 16 &&
-      sum_tc(D, P.kernel, P.d_ynodek.p, static_cast<int64_t>(D + 1) * P.n_pad, P.d_ynodek.p,
-             static_cast<int64_t>(D + 1) * P.n_pad, P.momq32.p, P.C, P.bqm32, P.loc32.p,
-             static_cast<int64_t>(kRC) * P.n_pad, P.d_far_rowptr.p, P.d_far_col.p, nullptr, 0, P.n, first,
-             P.C - first, P.n_pad, Rc, P.gauss_fact, P.d_err.p, P.stream))
-    return true;
+  P.m2l_engine = 1;
   SumArgs a{};
   a.tgt = P.d_ynodek.p;
   a.tgt_gstride = static_cast<int64_t>(D + 1) * P.n_pad;

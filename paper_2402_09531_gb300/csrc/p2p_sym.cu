@@ -65,8 +65,8 @@ namespace {
 using namespace tc;
 
 constexpr int kSymCompWarps = 16;
-constexpr int kSymThreads = (kSymCompWarps + 2) * 32;
-constexpr int kSymGThreads = (kSymCompWarps + 5) * 32;   // four MMA-issuing warps
+constexpr int kSymTcThreads = (kSymCompWarps + 3) * 32;  // forward and transposed issuers, TMA warp
+constexpr int kSymGThreads = (kSymCompWarps + 4) * 32;   // three MMA-issuing warps, one TMA warp
 constexpr int kChunk = 64;          // sources per chunk
 constexpr int kStages = 4;          // TMA stages (coordinates + FP16 charges of one chunk)
 constexpr int kTmemCols = 256;      // forward 2 entries x 2 tiles x 32, transposed 2 x 32
@@ -171,6 +171,47 @@ __device__ __forceinline__ void eval8x2(const float* sc, int j, const u64* xa, c
   }
 }
 
+// E' for one target (A) against sources j..j+7 (a) and j+8..j+15 (b) of
+// the stage: the one-tile (128-slot) form of eval8x2.
+template <int D, int KER>
+__device__ __forceinline__ void eval16x1(const float* sc, int j, const u64* xa, uint32_t* ha, uint32_t* la,
+                                         uint32_t* hb, uint32_t* lb) {
+  u64 pa[4], pb[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) pa[u] = pb[u] = 0ull;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    const ulonglong2 v0 = *reinterpret_cast<const ulonglong2*>(sc + k * kChunk + j);
+    const ulonglong2 v1 = *reinterpret_cast<const ulonglong2*>(sc + k * kChunk + j + 4);
+    const ulonglong2 w0 = *reinterpret_cast<const ulonglong2*>(sc + k * kChunk + j + 8);
+    const ulonglong2 w1 = *reinterpret_cast<const ulonglong2*>(sc + k * kChunk + j + 12);
+    if (KER == DWFMM_K_GAUSS) {
+      pa[0] = fma2(xa[k], v0.x, pa[0]); pa[1] = fma2(xa[k], v0.y, pa[1]);
+      pa[2] = fma2(xa[k], v1.x, pa[2]); pa[3] = fma2(xa[k], v1.y, pa[3]);
+      pb[0] = fma2(xa[k], w0.x, pb[0]); pb[1] = fma2(xa[k], w0.y, pb[1]);
+      pb[2] = fma2(xa[k], w1.x, pb[2]); pb[3] = fma2(xa[k], w1.y, pb[3]);
+    } else {
+      u64 df;
+      df = sub2(xa[k], v0.x); pa[0] = fma2(df, df, pa[0]);
+      df = sub2(xa[k], v0.y); pa[1] = fma2(df, df, pa[1]);
+      df = sub2(xa[k], v1.x); pa[2] = fma2(df, df, pa[2]);
+      df = sub2(xa[k], v1.y); pa[3] = fma2(df, df, pa[3]);
+      df = sub2(xa[k], w0.x); pb[0] = fma2(df, df, pb[0]);
+      df = sub2(xa[k], w0.y); pb[1] = fma2(df, df, pb[1]);
+      df = sub2(xa[k], w1.x); pb[2] = fma2(df, df, pb[2]);
+      df = sub2(xa[k], w1.y); pb[3] = fma2(df, df, pb[3]);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    float f0, f1;
+    up(pa[u], f0, f1);
+    split_f16x2(phi_sym<KER>(f0), phi_sym<KER>(f1), ha[u], la[u]);
+    up(pb[u], f0, f1);
+    split_f16x2(phi_sym<KER>(f0), phi_sym<KER>(f1), hb[u], lb[u]);
+  }
+}
+
 __device__ __forceinline__ void sts128(uint32_t addr, const uint32_t* v) {
   asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3])
                : "memory");
@@ -235,7 +276,7 @@ struct SymArgs {
 };
 
 template <int D, int KER>
-__global__ void __launch_bounds__(kSymThreads, 1) k_near_sym_tc(SymArgs a) {
+__global__ void __launch_bounds__(kSymTcThreads, 1) k_near_sym_tc(SymArgs a) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t bars[32];
   __shared__ uint32_t tmem_slot;
@@ -249,8 +290,8 @@ __global__ void __launch_bounds__(kSymThreads, 1) k_near_sym_tc(SymArgs a) {
   uint64_t* ffull = cready + 2;             // [2] forward accumulators of an entry complete (commit)
   uint64_t* fempty = ffull + 2;             // [2] forward accumulators folded (16 warps)
   uint64_t* qfull = fempty + 2;             // q_T landed
-  uint64_t* fin = qfull + 1;                // every MMA done
-  static_assert(2 * kStages + 16 <= 32, "barrier array");
+  uint64_t* fin = qfull + 1;                // [2] every MMA of an issuer done
+  static_assert(2 * kStages + 17 <= 32, "barrier array");
 
   const int ld = a.ld;
   const int NT = ld / 128;                    // 128-target tiles
@@ -277,7 +318,7 @@ __global__ void __launch_bounds__(kSymThreads, 1) k_near_sym_tc(SymArgs a) {
     }
     for (int i = 0; i < 2; ++i) {
       bar_init(&efull[i], kSymCompWarps);
-      bar_init(&efree[i], 1);
+      bar_init(&efree[i], 2);   // the forward and the transposed issuer
       bar_init(&tfull[i], 1);
       bar_init(&tempty[i], kSymCompWarps);
       bar_init(&cready[i], kSymCompWarps / 2);
@@ -285,7 +326,8 @@ __global__ void __launch_bounds__(kSymThreads, 1) k_near_sym_tc(SymArgs a) {
       bar_init(&fempty[i], kSymCompWarps);
     }
     bar_init(qfull, 1);
-    bar_init(fin, 1);
+    bar_init(&fin[0], 1);
+    bar_init(&fin[1], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) tmem_alloc(&tmem_slot, kTmemCols);
@@ -326,15 +368,53 @@ __global__ void __launch_bounds__(kSymThreads, 1) k_near_sym_tc(SymArgs a) {
         (void)wait_sleep(&full[j % kStages], static_cast<uint32_t>((j / kStages) & 1));
       if (bad) atomicExch(a.err, 3);
     }
-  } else if (warp == kSymCompWarps) {
-    // ---- MMA issuer
+  } else if (warp == kSymCompWarps + 2) {
+    // ---- transposed-product issuer (MMAs issued by two threads proceed
+    // concurrently; one thread's issue rate bounded the kernel)
     if (lane == 0) {
       bool bad = !wait_sleep(qfull, 0u);
-      const uint32_t ebase = sptr(ebuf), sbase = sptr(stages), qtb = sptr(qT);
+      const uint32_t ebase = sptr(ebuf), qtb = sptr(qT);
       int i = 0, jt = 0;
       for (int e = 0; e < ne && !bad; ++e) {
-        const int S = a.ups[e0 + e];
-        const bool diag = S == T;
+        const bool diag = a.ups[e0 + e] == T;
+        for (int c = 0; c < NC; ++c, ++i) {
+          const int eb = i & 1;
+          if (!wait_sleep(&efull[eb], static_cast<uint32_t>((i >> 1) & 1))) {
+            bad = true;
+            break;
+          }
+          if (!diag) {
+            const int tb = jt & 1;
+            if (jt >= 2 && !wait_sleep(&tempty[tb], static_cast<uint32_t>(((jt - 2) >> 1) & 1))) {
+              bad = true;
+              break;
+            }
+            fence_after();
+            const uint32_t et = ebase + eb * ebytes;
+            const uint32_t dcol = tmem + static_cast<uint32_t>(128 + tb * 32);
+            for (int j = 0; j < NT * 8; ++j) {
+              // A: rows [E_hi of 64 sources ; E_lo of 64 sources], MN-major
+              const u64 at = smem_desc(et + j * 2 * kTS, kSymTrnLbo, kSymTrnSbo);
+              const u64 bq = smem_desc(qtb + j * 2 * 512, 512, 128);
+              mma_f16(dcol, at, bq, kIdTrn32, j > 0 ? 1u : 0u);
+            }
+            mma_commit(&tfull[tb]);
+            ++jt;
+          }
+          mma_commit(&efree[eb]);
+        }
+      }
+      mma_commit(&fin[1]);
+      (void)wait_sleep(&fin[1], 0u);
+      if (bad) atomicExch(a.err, 3);
+    }
+  } else if (warp == kSymCompWarps) {
+    // ---- forward-product issuer
+    if (lane == 0) {
+      bool bad = false;
+      const uint32_t ebase = sptr(ebuf), sbase = sptr(stages);
+      int i = 0;
+      for (int e = 0; e < ne && !bad; ++e) {
         const int fb = e & 1;
         for (int c = 0; c < NC; ++c, ++i) {
           const int st = i % kStages, eb = i & 1;
@@ -359,30 +439,13 @@ __global__ void __launch_bounds__(kSymThreads, 1) k_near_sym_tc(SymArgs a) {
               mma_f16(dcol + 16, alo, bq, kIdFwd16, 1u);
             }
           }
-          if (!diag) {
-            const int tb = jt & 1;
-            if (jt >= 2 && !wait_sleep(&tempty[tb], static_cast<uint32_t>(((jt - 2) >> 1) & 1))) {
-              bad = true;
-              break;
-            }
-            fence_after();
-            const uint32_t dcol = tmem + static_cast<uint32_t>(128 + tb * 32);
-            for (int j = 0; j < NT * 8; ++j) {
-              // A: rows [E_hi of 64 sources ; E_lo of 64 sources], MN-major
-              const u64 at = smem_desc(et + j * 2 * kTS, kSymTrnLbo, kSymTrnSbo);
-              const u64 bq = smem_desc(qtb + j * 2 * 512, 512, 128);
-              mma_f16(dcol, at, bq, kIdTrn32, j > 0 ? 1u : 0u);
-            }
-            mma_commit(&tfull[tb]);
-            ++jt;
-          }
           mma_commit(&efree[eb]);
           mma_commit(&sfree[st]);
           if (c == NC - 1) mma_commit(&ffull[fb]);
         }
       }
-      mma_commit(fin);
-      (void)wait_sleep(fin, 0u);
+      mma_commit(&fin[0]);
+      (void)wait_sleep(&fin[0], 0u);
       if (bad) atomicExch(a.err, 3);
     }
   } else {
@@ -505,18 +568,27 @@ __global__ void __launch_bounds__(kSymThreads, 1) k_near_sym_tc(SymArgs a) {
         }
         const float* sc = reinterpret_cast<const float*>(stages + st * stage_bytes);
         const uint32_t et = sptr(ebuf + eb * ebytes);
+        if (NT == 2) {
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int j = part * 16 + h * 8;   // source within the chunk
-          uint32_t ha[4], la[4], hb[4], lb[4];
-          eval8x2<D, KER>(sc, j, xa, xb, ha, la, hb, lb);
-          const uint32_t off = static_cast<uint32_t>((ta >> 3) * kTS + (j >> 3) * 128 + (ta & 7) * 16);
-          sts128(et + off, ha);
-          sts128(et + off + kHL, la);
-          if (NT == 2) {
+          for (int h = 0; h < 2; ++h) {
+            const int j = part * 16 + h * 8;   // source within the chunk
+            uint32_t ha[4], la[4], hb[4], lb[4];
+            eval8x2<D, KER>(sc, j, xa, xb, ha, la, hb, lb);
+            const uint32_t off = static_cast<uint32_t>((ta >> 3) * kTS + (j >> 3) * 128 + (ta & 7) * 16);
+            sts128(et + off, ha);
+            sts128(et + off + kHL, la);
             sts128(et + off + 16 * kTS, hb);
             sts128(et + off + 16 * kTS + kHL, lb);
           }
+        } else {   // one tile: the thread's target against 16 sources
+          const int j = part * 16;
+          uint32_t ha[4], la[4], hb[4], lb[4];
+          eval16x1<D, KER>(sc, j, xa, ha, la, hb, lb);
+          const uint32_t off = static_cast<uint32_t>((ta >> 3) * kTS + (j >> 3) * 128 + (ta & 7) * 16);
+          sts128(et + off, ha);
+          sts128(et + off + kHL, la);
+          sts128(et + off + 128, hb);
+          sts128(et + off + 128 + kHL, lb);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncwarp();
@@ -558,8 +630,9 @@ __global__ void __launch_bounds__(kSymThreads, 1) k_near_sym_tc(SymArgs a) {
 }
 
 // Per right-hand side: the largest |q * factor| (float bits, atomicMax).
-__global__ void k_sym_colmax(const float* xb, const float* pts, int64_t gstride, int L, int ld, int D, int gauss,
-                             int Rc, unsigned* colmax) {
+// Charges xb[g][r][s] with row stride xld; slots s >= nvalid hold none.
+__global__ void k_sym_colmax(const float* xb, int64_t xld, int nvalid, const float* pts, int64_t gstride, int L,
+                             int ld, int D, int gauss, int Rc, unsigned* colmax) {
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   const int64_t n = static_cast<int64_t>(L) * ld;
   float m[16];
@@ -568,8 +641,9 @@ __global__ void k_sym_colmax(const float* xb, const float* pts, int64_t gstride,
   for (int64_t p = i; p < n; p += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const int64_t g = p / ld;
     const int s = static_cast<int>(p % ld);
+    if (s >= nvalid) continue;
     const float f = gauss ? exp2f(-pts[g * gstride + static_cast<int64_t>(D) * ld + s]) : 1.0f;
-    for (int r = 0; r < Rc; ++r) m[r] = fmaxf(m[r], fabsf(xb[(g * 16 + r) * ld + s] * f));
+    for (int r = 0; r < Rc; ++r) m[r] = fmaxf(m[r], fabsf(xb[(g * 16 + r) * xld + s] * f));
   }
   for (int r = 0; r < Rc; ++r) {
     float v = m[r];
@@ -590,8 +664,8 @@ __device__ __forceinline__ float col_scale_exp(unsigned bits, int* e) {
 // FP16 hi / lo charge blocks: q' = q * factor * 2^-e_r, core (s/8, n/8) at
 // (s/8)*512 + (n/8)*128, row n%8 at 16 bytes, source s%8 at 2 bytes; n < 16
 // hi, n >= 16 lo.
-__global__ void k_sym_make_bq(const float* xb, const float* pts, int64_t gstride, int L, int ld, int D, int gauss,
-                              int Rc, const unsigned* colmax, uint16_t* bq) {
+__global__ void k_sym_make_bq(const float* xb, int64_t xld, int nvalid, const float* pts, int64_t gstride, int L,
+                              int ld, int D, int gauss, int Rc, const unsigned* colmax, uint16_t* bq) {
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= static_cast<int64_t>(L) * ld * 16) return;
   const int r = static_cast<int>(i % 16);
@@ -599,11 +673,11 @@ __global__ void k_sym_make_bq(const float* xb, const float* pts, int64_t gstride
   const int s = static_cast<int>(gs % ld);
   const int64_t g = gs / ld;
   float v = 0.0f;
-  if (r < Rc) {
+  if (r < Rc && s < nvalid) {
     int ex;
     const float sc = col_scale_exp(colmax[r], &ex);
     const float f = gauss ? exp2f(-pts[g * gstride + static_cast<int64_t>(D) * ld + s]) : 1.0f;
-    v = xb[(g * 16 + r) * ld + s] * f * sc;
+    v = xb[(g * 16 + r) * xld + s] * f * sc;
   }
   const __half h = __float2half_rn(v);
   const __half l = __float2half_rn((v - __half2float(h)) * kLoScale);
@@ -613,22 +687,23 @@ __global__ void k_sym_make_bq(const float* xb, const float* pts, int64_t gstride
   blk[base + (2 + r / 8) * 64 + (r % 8) * 8] = __half_as_ushort(l);
 }
 
-// y_near = (forward + fixed-point transposed) * 2^e_r * factor(t).
+// y = (forward + fixed-point transposed) * 2^e_r * factor(t), written to
+// y[g * ystride + r * yrow + s] for slots s < nvalid.
 __global__ void k_sym_finish(const float* fwd, const unsigned long long* acc, double inv_scale, const float* pts,
                              int64_t gstride, int L, int ld, int D, int gauss, int Rc, const unsigned* colmax,
-                             float* ynear, int64_t ystride) {
+                             float* ynear, int64_t ystride, int64_t yrow, int nvalid) {
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= static_cast<int64_t>(L) * 16 * ld) return;
   const int s = static_cast<int>(i % ld);
   const int r = static_cast<int>((i / ld) % 16);
   const int64_t g = i / (16 * static_cast<int64_t>(ld));
-  if (r >= Rc) return;
+  if (r >= Rc || s >= nvalid) return;
   int ex;
   (void)col_scale_exp(colmax[r], &ex);
   const double tr = static_cast<double>(static_cast<long long>(acc[i])) * inv_scale;
   double v = (static_cast<double>(fwd[i]) + tr) * ldexp(1.0, ex);
   if (gauss) v *= static_cast<double>(exp2f(-pts[g * gstride + static_cast<int64_t>(D) * ld + s]));
-  ynear[g * ystride + static_cast<int64_t>(r) * ld + s] = static_cast<float>(v);
+  ynear[g * ystride + static_cast<int64_t>(r) * yrow + s] = static_cast<float>(v);
 }
 
 // ---------------------------------------------------------------------------
@@ -707,7 +782,7 @@ __global__ void __launch_bounds__(kSymGThreads, 1) k_near_sym_gtc(SymGArgs a) {
   uint64_t* gfull = fempty + 2;             // [2] G of a chunk complete
   uint64_t* gfree = gfull + 2;              // [2] G read by the compute warps (16 warps)
   uint64_t* qfull = gfree + 2;              // q_T and 2x'_T landed
-  uint64_t* fin = qfull + 1;                // [4] all MMAs of an issuer complete
+  uint64_t* fin = qfull + 1;                // [4] all MMAs of an issuer complete (3 used)
   static_assert(2 * kStages + 23 <= 32, "barrier array");
 
   const int ld = a.ld;              // 256: two 128-target tiles, four 64-source chunks
@@ -730,16 +805,16 @@ __global__ void __launch_bounds__(kSymGThreads, 1) k_near_sym_gtc(SymGArgs a) {
 
   if (t == 0) {
     // barriers the MMAs complete count one commit of each issuer that uses
-    // the resource: the stage and G (two G/forward issuers), the E tile (all
-    // four), the transposed accumulators (two transposed issuers)
+    // the resource: the stage and G (two G / forward issuers), the E tile
+    // (all three), the transposed accumulators (the transposed issuer)
     for (int i = 0; i < kStages; ++i) {
       bar_init(&full[i], 1);
       bar_init(&sfree[i], 2);
     }
     for (int i = 0; i < 2; ++i) {
       bar_init(&efull[i], kSymCompWarps);
-      bar_init(&efree[i], 4);
-      bar_init(&tfull[i], 2);
+      bar_init(&efree[i], 3);
+      bar_init(&tfull[i], 1);
       bar_init(&tempty[i], kSymCompWarps);
       bar_init(&cready[i], kSymCompWarps / 2);
       bar_init(&ffull[i], 2);
@@ -790,11 +865,12 @@ __global__ void __launch_bounds__(kSymGThreads, 1) k_near_sym_gtc(SymGArgs a) {
         (void)wait_sleep(&full[j % kStages], static_cast<uint32_t>((j / kStages) & 1));
       if (bad) atomicExch(a.err, 3);
     }
-  } else if (warp >= kSymCompWarps + 3) {
-    // ---- transposed-product issuers, one per target tile (its K half of
-    // E^T q_T), beside the G / forward issuers: MMAs issued by several
-    // threads proceed concurrently, one thread's issue rate bounded the kernel
-    const int at = warp - (kSymCompWarps + 3);
+  } else if (warp == kSymCompWarps + 3) {
+    // ---- transposed-product issuer (E^T q_T over both target tiles, one K
+    // half per TMEM accumulator), beside the two G / forward issuers: MMAs
+    // issued by several threads proceed concurrently, and one thread's issue
+    // rate bounded the kernel.  Three issuers and one TMA warp leave 96
+    // registers per thread (a fourth issuer forced spills and was slower)
     if (lane == 0) {
       bool bad = !wait_sleep(qfull, 0u);
       const u64 dT_a = smem_desc(sptr(ebuf), kSymTrnLbo, kSymTrnSbo);   // E tile 0, transposed A
@@ -815,12 +891,15 @@ __global__ void __launch_bounds__(kSymGThreads, 1) k_near_sym_gtc(SymGArgs a) {
               break;
             }
             fence_after();
-            const uint32_t dcol = tmem + (at == 0 ? kTr : kTr1) + static_cast<uint32_t>(tb * 32);
             const u64 ta = dT_a + ((eb * ebytes) >> 4);
 #pragma unroll
-            for (int jj = 0; jj < 8; ++jj) {
-              const int j = 8 * at + jj;
-              mma_f16(dcol, ta + ((j * 2 * kTS) >> 4), dT_b + ((j * 2 * 512) >> 4), kIdTrn32, jj > 0 ? 1u : 0u);
+            for (int h = 0; h < 2; ++h) {
+              const uint32_t dcol = tmem + (h == 0 ? kTr : kTr1) + static_cast<uint32_t>(tb * 32);
+#pragma unroll
+              for (int jj = 0; jj < 8; ++jj) {
+                const int j = 8 * h + jj;
+                mma_f16(dcol, ta + ((j * 2 * kTS) >> 4), dT_b + ((j * 2 * 512) >> 4), kIdTrn32, jj > 0 ? 1u : 0u);
+              }
             }
             mma_commit(&tfull[tb]);
             ++jt;
@@ -828,8 +907,8 @@ __global__ void __launch_bounds__(kSymGThreads, 1) k_near_sym_gtc(SymGArgs a) {
           mma_commit(&efree[eb]);
         }
       }
-      mma_commit(&fin[2 + at]);
-      (void)wait_sleep(&fin[2 + at], 0u);
+      mma_commit(&fin[2]);
+      (void)wait_sleep(&fin[2], 0u);
       if (bad) atomicExch(a.err, 3);
     }
   } else if (warp == kSymCompWarps || warp == kSymCompWarps + 2) {
@@ -1092,9 +1171,9 @@ size_t sym_smem(int D, int ld) {
 template <int D>
 void sym_launch_d(int kernel, const SymArgs& a, int grid, size_t smem, cudaStream_t s) {
   switch (kernel) {
-    case DWFMM_K_EXP: k_near_sym_tc<D, DWFMM_K_EXP><<<grid, kSymThreads, smem, s>>>(a); break;
-    case DWFMM_K_MATERN32: k_near_sym_tc<D, DWFMM_K_MATERN32><<<grid, kSymThreads, smem, s>>>(a); break;
-    default: k_near_sym_tc<D, DWFMM_K_GAUSS><<<grid, kSymThreads, smem, s>>>(a);
+    case DWFMM_K_EXP: k_near_sym_tc<D, DWFMM_K_EXP><<<grid, kSymTcThreads, smem, s>>>(a); break;
+    case DWFMM_K_MATERN32: k_near_sym_tc<D, DWFMM_K_MATERN32><<<grid, kSymTcThreads, smem, s>>>(a); break;
+    default: k_near_sym_tc<D, DWFMM_K_GAUSS><<<grid, kSymTcThreads, smem, s>>>(a);
   }
 }
 
@@ -1148,21 +1227,49 @@ int sym_tc_bits(const Plan& P) {
   return 62 - static_cast<int>(std::ceil(std::log2(bound)));
 }
 
+namespace {
+
+void ensure_sym_attrs() {
+  const uint64_t dbit = device_bit();
+  if (g_sym_attrs_dev.load() & dbit) return;
+  sym_attrs_d<4>(kSymSmemMax);
+  sym_attrs_d<8>(kSymSmemMax);
+  sym_attrs_d<10>(kSymSmemMax);
+  sym_attrs_d<12>(kSymSmemMax);
+  sym_attrs_d<16>(kSymSmemMax);
+  sym_attrs_d<20>(kSymSmemMax);
+  cudaFuncSetAttribute(k_near_sym_gtc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSymSmemMax);
+  DW_CUDA(cudaGetLastError());
+  g_sym_attrs_dev.fetch_or(dbit);
+}
+
+void launch_sym_tc(int D, int kernel, const SymArgs& a, int grid, size_t smem, cudaStream_t s) {
+  switch (D) {
+    case 4: sym_launch_d<4>(kernel, a, grid, smem, s); break;
+    case 8: sym_launch_d<8>(kernel, a, grid, smem, s); break;
+    case 10: sym_launch_d<10>(kernel, a, grid, smem, s); break;
+    case 12: sym_launch_d<12>(kernel, a, grid, smem, s); break;
+    case 16: sym_launch_d<16>(kernel, a, grid, smem, s); break;
+    default: sym_launch_d<20>(kernel, a, grid, smem, s); break;
+  }
+}
+
+// Node coordinates of every cluster in 128-slot blocks: [C][D+1][128] from
+// the scaled node blocks [C][D+1][n_pad] (row D = |y'|^2), slots >= n_pad zero.
+__global__ void k_m2l_crd(const float* ynodek, int C, int D, int np, float* out) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= static_cast<int64_t>(C) * (D + 1) * 128) return;
+  const int a = static_cast<int>(i & 127);
+  const int64_t row = i >> 7;
+  out[i] = a < np ? ynodek[row * np + a] : 0.0f;
+}
+
+}  // namespace
+
 bool near_sym_tc(Plan& P, int D, int Rc, cudaStream_t s) {
   const int RC = 16;
   if (!sym_tc_eligible(P, D, RC)) return false;
-  const uint64_t dbit = device_bit();
-  if (!(g_sym_attrs_dev.load() & dbit)) {
-    sym_attrs_d<4>(kSymSmemMax);
-    sym_attrs_d<8>(kSymSmemMax);
-    sym_attrs_d<10>(kSymSmemMax);
-    sym_attrs_d<12>(kSymSmemMax);
-    sym_attrs_d<16>(kSymSmemMax);
-    sym_attrs_d<20>(kSymSmemMax);
-    cudaFuncSetAttribute(k_near_sym_gtc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSymSmemMax);
-    DW_CUDA(cudaGetLastError());
-    g_sym_attrs_dev.fetch_or(dbit);
-  }
+  ensure_sym_attrs();
   const int ld = P.m_pad;
   const int64_t nsite = static_cast<int64_t>(P.L) * 16 * ld;
   const int64_t gstride = static_cast<int64_t>(D + 1) * ld;
@@ -1173,10 +1280,10 @@ bool near_sym_tc(Plan& P, int D, int Rc, cudaStream_t s) {
   P.sym_colmax.alloc(16);
   DW_CUDA(cudaMemsetAsync(P.sym_colmax.p, 0, 16 * sizeof(unsigned), s));
   DW_CUDA(cudaMemsetAsync(P.sym_acc.p, 0, static_cast<size_t>(nsite) * sizeof(unsigned long long), s));
-  k_sym_colmax<<<2 * sm_count(), 256, 0, s>>>(P.xb32.p, P.d_ptsk.p, gstride, P.L, ld, D, gauss, Rc,
+  k_sym_colmax<<<2 * sm_count(), 256, 0, s>>>(P.xb32.p, ld, ld, P.d_ptsk.p, gstride, P.L, ld, D, gauss, Rc,
                                                P.sym_colmax.p);
   k_sym_make_bq<<<ceil_div(static_cast<int64_t>(P.L) * ld * 16, 256), 256, 0, s>>>(
-      P.xb32.p, P.d_ptsk.p, gstride, P.L, ld, D, gauss, Rc, P.sym_colmax.p, P.sym_bq16.p);
+      P.xb32.p, ld, ld, P.d_ptsk.p, gstride, P.L, ld, D, gauss, Rc, P.sym_colmax.p, P.sym_bq16.p);
   const int sb = sym_tc_bits(P);
   if (sym_g_applies(P, D)) {
     P.near_engine = 5;
@@ -1203,7 +1310,7 @@ bool near_sym_tc(Plan& P, int D, int Rc, cudaStream_t s) {
     DW_CUDA(cudaGetLastError());
     k_sym_finish<<<ceil_div(nsite, 256), 256, 0, s>>>(P.sym_fwd.p, P.sym_acc.p, std::ldexp(1.0, -sb), P.d_ptsk.p,
                                                        gstride, P.L, ld, D, gauss, Rc, P.sym_colmax.p, P.ynear32.p,
-                                                       static_cast<int64_t>(kRC) * ld);
+                                                       static_cast<int64_t>(kRC) * ld, ld, ld);
     DW_CUDA(cudaGetLastError());
     return true;
   }
@@ -1219,19 +1326,78 @@ bool near_sym_tc(Plan& P, int D, int Rc, cudaStream_t s) {
   a.acc_scale = std::ldexp(1.0f, sb);
   a.ld = ld;
   a.err = P.d_err.p;
-  const size_t smem = sym_smem(D, ld);
-  switch (D) {
-    case 4: sym_launch_d<4>(P.kernel, a, P.L, smem, s); break;
-    case 8: sym_launch_d<8>(P.kernel, a, P.L, smem, s); break;
-    case 10: sym_launch_d<10>(P.kernel, a, P.L, smem, s); break;
-    case 12: sym_launch_d<12>(P.kernel, a, P.L, smem, s); break;
-    case 16: sym_launch_d<16>(P.kernel, a, P.L, smem, s); break;
-    default: sym_launch_d<20>(P.kernel, a, P.L, smem, s); break;
-  }
+  launch_sym_tc(D, P.kernel, a, P.L, sym_smem(D, ld), s);
   DW_CUDA(cudaGetLastError());
   k_sym_finish<<<ceil_div(nsite, 256), 256, 0, s>>>(P.sym_fwd.p, P.sym_acc.p, std::ldexp(1.0, -sb), P.d_ptsk.p,
                                                      gstride, P.L, ld, D, gauss, Rc, P.sym_colmax.p, P.ynear32.p,
-                                                     static_cast<int64_t>(kRC) * ld);
+                                                     static_cast<int64_t>(kRC) * ld, ld, ld);
+  DW_CUDA(cudaGetLastError());
+  return true;
+}
+
+// The couplings (M2L, Eq. (5.4)) of MIXED plans with 9..16 right-hand sides
+// on the symmetric engine: the far list holds both orderings of every
+// admissible pair of clusters and K is symmetric, so each unordered pair
+// (t, s > t) is evaluated once, targets = the nodes of t, sources = the
+// nodes of s, charges = the moments m_s; the forward sums go to t, the
+// transposed ones (fixed point, order independent) to s.  Node sets are
+// padded to 128 slots (zero charges); only the levels with far blocks are
+// touched (the moments of coarser clusters are never computed).  Returns
+// false where the path does not apply (the ordered-pair engines run
+// instead).
+bool m2l_sym_tc(Plan& P, int D, int Rc, cudaStream_t s) {
+  if (P.prec != DWFMM_P_MIXED || Rc < 9 || Rc > 16 || !P.fsym_ok || P.fsym_rows <= 0) return false;
+  if (P.n_pad > 128 || (D != 4 && D != 8 && D != 10 && D != 12 && D != 16 && D != 20)) return false;
+  if (P.kernel == DWFMM_K_GAUSS && !(P.gauss_fact && 2.0 * P.gauss_bound <= 15.0)) return false;
+  if (sym_smem(D, 128) > static_cast<size_t>(kSymSmemMax) || !P.d_ynodek.p || P.dpad != D) return false;
+  ensure_sym_attrs();
+  const int C = P.C, ld = 128, np = P.n_pad;
+  const int64_t gstride = static_cast<int64_t>(D + 1) * ld;
+  const int64_t nslot = static_cast<int64_t>(C) * 16 * ld;
+  const int gauss = P.kernel == DWFMM_K_GAUSS ? 1 : 0;
+  if (P.m2l_crd_D != D || !P.m2l_crd.p) {
+    P.m2l_crd.alloc(static_cast<size_t>(C) * gstride);
+    k_m2l_crd<<<ceil_div(static_cast<int64_t>(C) * gstride, 256), 256, 0, s>>>(P.d_ynodek.p, C, D, np,
+                                                                             P.m2l_crd.p);
+    P.m2l_crd_D = D;
+  }
+  P.m2l_bq16.alloc(static_cast<size_t>(C) * ld * 32);
+  P.m2l_acc.alloc(static_cast<size_t>(nslot));
+  P.m2l_fwd.alloc(static_cast<size_t>(nslot));
+  P.m2l_colmax.alloc(16);
+  DW_CUDA(cudaMemsetAsync(P.m2l_colmax.p, 0, 16 * sizeof(unsigned), s));
+  DW_CUDA(cudaMemsetAsync(P.m2l_acc.p, 0, static_cast<size_t>(nslot) * sizeof(unsigned long long), s));
+  // targets without upper entries get no CTA; their forward sums stay zero
+  DW_CUDA(cudaMemsetAsync(P.m2l_fwd.p, 0, static_cast<size_t>(nslot) * sizeof(float), s));
+  // only the clusters of the levels with far blocks (>= jmin) carry moments
+  const int first = (1 << P.jmin) - 1, nc = C - first;
+  const float* mom = P.mom32.p + static_cast<int64_t>(first) * 16 * np;
+  const float* crd = P.m2l_crd.p + static_cast<int64_t>(first) * gstride;
+  k_sym_colmax<<<2 * sm_count(), 256, 0, s>>>(mom, np, P.n, crd, gstride, nc, ld, D, gauss, Rc, P.m2l_colmax.p);
+  k_sym_make_bq<<<ceil_div(static_cast<int64_t>(nc) * ld * 16, 256), 256, 0, s>>>(
+      mom, np, P.n, crd, gstride, nc, ld, D, gauss, Rc, P.m2l_colmax.p,
+      P.m2l_bq16.p + static_cast<int64_t>(first) * ld * 32);
+  // fixed-point bits: a partial sum is at most (all nodes) x E'max x max |q'|
+  const double emax = gauss ? std::exp2(2.0 * P.gauss_bound) : 1.0;
+  const int sb = 62 - static_cast<int>(std::ceil(std::log2(static_cast<double>(C) * ld * emax * 2.0)));
+  SymArgs a{};
+  a.pts = P.m2l_crd.p;
+  a.gstride = gstride;
+  a.bq = P.m2l_bq16.p;
+  a.uprow = P.fsym_uprow.p;
+  a.ups = P.fsym_s.p;
+  a.order = P.fsym_order.p;
+  a.fwd = P.m2l_fwd.p;
+  a.acc = P.m2l_acc.p;
+  a.acc_scale = std::ldexp(1.0f, sb);
+  a.ld = ld;
+  a.err = P.d_err.p;
+  launch_sym_tc(D, P.kernel, a, P.fsym_rows, sym_smem(D, ld), s);
+  DW_CUDA(cudaGetLastError());
+  const int64_t off = static_cast<int64_t>(first) * 16 * ld;
+  k_sym_finish<<<ceil_div(static_cast<int64_t>(nc) * 16 * ld, 256), 256, 0, s>>>(
+      P.m2l_fwd.p + off, P.m2l_acc.p + off, std::ldexp(1.0, -sb), crd, gstride, nc, ld, D, gauss, Rc,
+      P.m2l_colmax.p, P.loc32.p + static_cast<int64_t>(first) * 16 * np, static_cast<int64_t>(kRC) * np, np, np);
   DW_CUDA(cudaGetLastError());
   return true;
 }

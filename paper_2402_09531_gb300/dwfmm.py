@@ -32,7 +32,8 @@ PHASES = ("gather", "p2m_m2m", "m2l", "l2l_l2p", "p2p", "scatter", "matvec")
 # Every entry point declared in include/dwfmm.h.
 EXPORTS = ("dwfmm_plan_create", "dwfmm_plan_set_nodes", "dwfmm_tree_build", "dwfmm_matvec",
            "dwfmm_solve", "dwfmm_plan_destroy", "dwfmm_status_string", "dwfmm_last_error",
-           "dwfmm_plan_info", "dwfmm_near_engine", "dwfmm_far_engine", "dwfmm_plan_export", "dwfmm_tree_export", "dwfmm_lists_export",
+           "dwfmm_plan_info", "dwfmm_near_engine", "dwfmm_far_engine", "dwfmm_m2l_engine",
+           "dwfmm_plan_set_m2l_engine", "dwfmm_m2l_tune_ms", "dwfmm_plan_export", "dwfmm_tree_export", "dwfmm_lists_export",
            "dwfmm_set_profiling", "dwfmm_phase_times", "dwfmm_direct_sum_noalloc",
            "dwfmm_cg_begin", "dwfmm_cg_step", "dwfmm_cg_poll", "dwfmm_cg_result", "dwfmm_residual",
            "dwfmm_refine",
@@ -75,6 +76,9 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "dwfmm_plan_info": (i32, [P, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), C.POINTER(i32)]),
         "dwfmm_near_engine": (i32, [P, C.POINTER(i32)]),
         "dwfmm_far_engine": (i32, [P, C.POINTER(i32)]),
+        "dwfmm_m2l_engine": (i32, [P, C.POINTER(i32)]),
+        "dwfmm_plan_set_m2l_engine": (i32, [P, i32]),
+        "dwfmm_m2l_tune_ms": (i32, [P, P]),
         "dwfmm_plan_export": (i32, [P, P, P, P, P, P]),
         "dwfmm_tree_export": (i32, [P, P, P, P, P, P]),
         "dwfmm_lists_export": (i32, [P, P, P]),
@@ -353,6 +357,27 @@ class Plan:
         e = C.c_int32(-1)
         self.check(self._l.dwfmm_far_engine(self.h, C.byref(e)))
         return self.FAR_ENGINES.get(int(e.value), str(e.value))
+
+    M2L_ENGINES = {-1: "none", 0: "fp64_cuda_cores", 1: "fp32_cuda_cores", 2: "mixed_tf32_tensor",
+                   3: "mixed_symmetric_fp16_tensor"}
+
+    def m2l_engine(self) -> str:
+        """Engine that ran the couplings (M2L) in the last matvec."""
+        e = C.c_int32(-1)
+        self.check(self._l.dwfmm_m2l_engine(self.h, C.byref(e)))
+        return self.M2L_ENGINES.get(int(e.value), str(e.value))
+
+    def set_m2l_engine(self, engine: str = "auto"):
+        """M2L engine of MIXED matvecs with 9..16 right-hand sides: "auto"
+        (timed once per tree), "mixed_tf32_tensor" or "mixed_symmetric_fp16_tensor"."""
+        code = {"auto": -1, "mixed_tf32_tensor": 2, "mixed_symmetric_fp16_tensor": 3}[engine]
+        self.check(self._l.dwfmm_plan_set_m2l_engine(self.h, code))
+
+    def m2l_tune_ms(self):
+        """(symmetric, ordered) M2L times of the per-tree timing, -1 where not timed."""
+        ms = (C.c_double * 2)()
+        self.check(self._l.dwfmm_m2l_tune_ms(self.h, ms))
+        return float(ms[0]), float(ms[1])
 
     def export_expansion(self):
         n, d = self.n_x, self.d

@@ -6,7 +6,8 @@ within the float32 tolerance and the float64 GPU matvec of the same plan
 parameters far tighter (the hi/lo split carries ~2^-22 relative per
 element, the level of the float32 CUDA-core path), repeat bit-identically,
 and handle ragged leaves, fewer than 16 right-hand sides and several
-16-column passes."""
+16-column passes.  These cases force the symmetric M2L (each unordered far
+pair once) where it applies; the last test checks the timed default."""
 import numpy as np
 import pytest
 
@@ -27,11 +28,12 @@ def built():
     ge.build()
 
 
-def _run(w, X, f, pb, precision):
+def _run(w, X, f, pb, precision, m2l="mixed_symmetric_fp16_tensor"):
     import torch
     from paper_2402_09531_gb300 import Plan
     plan = Plan(d=w.d, kernel=w.kernel, sigma=w.sigma, gamma=w.gamma, q=w.q, eta=w.eta, leaf_size=w.leaf,
                 precision=precision, max_rhs=max(1, f.shape[0]))
+    plan.set_m2l_engine(m2l)
     plan.set_nodes(pb.exp_.nodes)
     plan.tree_build(torch.from_numpy(X).cuda())
     xd = torch.from_numpy(f).cuda()
@@ -62,6 +64,10 @@ def test_tensor_core_far_field_matches_oracle_and_fp64(base, n, leaf, nrhs, q, e
     plan, xd, yd = _run(w, X, f, pb, "mixed")
     assert plan.far_engine() == "mixed_fp16_tensor"
     assert plan.info()[1] > 0            # the far field is not empty
+    # a pass of 9..16 right-hand sides: each unordered far pair once (M2L);
+    # the engine reported is the last pass's
+    last = nrhs % 16 or 16
+    assert plan.m2l_engine() == ("mixed_symmetric_fp16_tensor" if last >= 9 else "fp32_cuda_cores")
     y = yd.cpu().numpy()
     assert np.all(np.isfinite(y))
     assert o.rel_err(y, o.fmm_matvec(pb, f)) <= FP32_TOL
@@ -117,3 +123,32 @@ def test_far_field_alone_against_oracle_expansion():
     assert np.linalg.norm(ref) > 0
     assert o.rel_err(y, ref) <= FP32_TOL
     plan.close()
+
+
+@pytest.mark.parametrize("leaf,n", [(256, 5000), (128, 6000)])
+def test_m2l_engines_agree_and_the_default_is_timed(leaf, n):
+    """Both tensor-core M2L engines (every ordered far pair; each unordered
+    pair once) match the oracle; the default times both at the first
+    matvec of the tree and runs the faster, reporting the two times.  The
+    first case has far blocks at a coarse level (jmin = 3 of 5) whose
+    parents never get moments."""
+    b = di.small_exp_d4()
+    w = di.scaled(b, n, nrhs=16)
+    w.seed, w.leaf = 57, leaf
+    X, f = di.sites_and_rhs(w)
+    pb = o.make_problem(X, w.kernel, o.weights_inv_gamma(w.gamma), w.q, w.leaf, w.eta)
+    ref = o.fmm_matvec(pb, f)
+    outs = {}
+    for eng in ("mixed_tf32_tensor", "mixed_symmetric_fp16_tensor", "auto"):
+        plan, _, yd = _run(w, X, f, pb, "mixed", m2l=eng)
+        got = plan.m2l_engine()
+        if eng == "auto":
+            ms = plan.m2l_tune_ms()
+            assert ms[0] > 0 and ms[1] > 0, ms
+            assert got == ("mixed_symmetric_fp16_tensor" if ms[0] < ms[1] else "mixed_tf32_tensor")
+        else:
+            assert got == eng
+        outs[eng] = yd.cpu().numpy()
+        assert o.rel_err(outs[eng], ref) <= FP32_TOL
+        plan.close()
+    assert o.rel_err(outs["mixed_tf32_tensor"], outs["mixed_symmetric_fp16_tensor"]) <= 2 * FP32_TOL
