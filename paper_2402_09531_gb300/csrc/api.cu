@@ -89,6 +89,9 @@ void Plan::free_tree() {
   fsym_ok = false;
   m2l_crd.release();
   m2l_crd_D = -1;
+  m2l_xa16.release();
+  m2l_xb16.release();
+  m2l_x16_D = -1;
   m2l_bq16.release();
   m2l_fwd.release();
   m2l_acc.release();

@@ -306,6 +306,8 @@ struct Plan {
   bool fsym_ok = false;
   DBuf<float> m2l_crd;
   int m2l_crd_D = -1;
+  DBuf<uint16_t> m2l_xa16, m2l_xb16;   // FP16 hi/lo node coordinates (2y', y') of the Gaussian path
+  int m2l_x16_D = -1;
   DBuf<uint16_t> m2l_bq16;
   DBuf<float> m2l_fwd;
   DBuf<unsigned long long> m2l_acc;

@@ -728,7 +728,6 @@ __global__ void k_sym_finish(const float* fwd, const unsigned long long* acc, do
 
 constexpr int kKD = 16;                                  // padded dimension of the G contraction
 constexpr uint32_t kIdG = idesc_f16(128, 64, 0);
-constexpr int kXBytesLeaf256 = 2 * 256 * kKD * 2;        // 16 KB
 constexpr int kXChunkHalf = (kChunk / 8) * (kKD / 8) * 128;   // 2 KB: one of hi / lo of a chunk
 
 // hi / lo FP16 coordinate blocks: xa = 2x' (target role), xb = x' (source role)
@@ -766,6 +765,8 @@ struct SymGArgs {
   int* err;
 };
 
+// NT target tiles of 128 (leaves of 256 slots: NT = 2; node sets of 128: NT = 1).
+template <int NT>
 __global__ void __launch_bounds__(kSymGThreads, 1) k_near_sym_gtc(SymGArgs a) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t bars[32];
@@ -785,23 +786,28 @@ __global__ void __launch_bounds__(kSymGThreads, 1) k_near_sym_gtc(SymGArgs a) {
   uint64_t* fin = qfull + 1;                // [4] all MMAs of an issuer complete (3 used)
   static_assert(2 * kStages + 23 <= 32, "barrier array");
 
-  const int ld = a.ld;              // 256: two 128-target tiles, four 64-source chunks
-  constexpr int NT = 2, NC = 4;
+  constexpr int ld = 128 * NT;      // NT 128-target tiles, 2 NT 64-source chunks
+  constexpr int NC = 2 * NT;
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int T = a.order[blockIdx.x];
   const int e0 = a.uprow[T], ne = a.uprow[T + 1] - e0;
   const int nchunks = ne * NC;
 
-  constexpr uint32_t ebytes = NT * 16 * kTS;                         // 64 KB
+  constexpr uint32_t ebytes = NT * 16 * kTS;                         // 32 KB per tile
   constexpr uint32_t stage_bytes = 2 * kXChunkHalf + kQChunkBytes;  // 8 KB
   unsigned char* ebuf = smem;
   unsigned char* stages = smem + 2 * ebytes;
-  unsigned char* qT = stages + kStages * stage_bytes;               // 16 KB
-  unsigned char* xT = qT + ld * 64;                                  // 16 KB
-  float* comb = reinterpret_cast<float*>(xT + kXBytesLeaf256);      // [2][16][64]
-  // TMEM column bases: G, forward accumulators, transposed accumulators of
-  // the two issuers (target tile 0 and 1: the two K halves of E^T q_T)
-  constexpr uint32_t kG = 0, kF = 256, kTr = 384, kTr1 = 448;
+  constexpr uint32_t xbytes = ld * kKD * 2 * 2;                     // target coordinates, hi and lo
+  unsigned char* qT = stages + kStages * stage_bytes;               // ld * 64 bytes
+  unsigned char* xT = qT + ld * 64;                                  // ld * 64 bytes
+  float* comb = reinterpret_cast<float*>(xT + xbytes);              // [2][16][64]
+  // TMEM column bases: G (2 buffers x NT tiles x 64), forward accumulators
+  // (2 x NT x 32), transposed accumulators (2 x 32 per K half: one half per
+  // target tile)
+  constexpr uint32_t kGB = NT * 64, kFB = NT * 32;
+  constexpr uint32_t kG = 0, kF = 2 * kGB, kTr = kF + 2 * kFB, kTr1 = kTr + 64;
+  constexpr uint32_t kCols = NT == 2 ? 512 : 256;
+  static_assert(kTr + 64 * NT <= kCols, "TMEM columns");
 
   if (t == 0) {
     // barriers the MMAs complete count one commit of each issuer that uses
@@ -809,24 +815,24 @@ __global__ void __launch_bounds__(kSymGThreads, 1) k_near_sym_gtc(SymGArgs a) {
     // (all three), the transposed accumulators (the transposed issuer)
     for (int i = 0; i < kStages; ++i) {
       bar_init(&full[i], 1);
-      bar_init(&sfree[i], 2);
+      bar_init(&sfree[i], NT);
     }
     for (int i = 0; i < 2; ++i) {
       bar_init(&efull[i], kSymCompWarps);
-      bar_init(&efree[i], 3);
+      bar_init(&efree[i], NT + 1);
       bar_init(&tfull[i], 1);
       bar_init(&tempty[i], kSymCompWarps);
       bar_init(&cready[i], kSymCompWarps / 2);
-      bar_init(&ffull[i], 2);
+      bar_init(&ffull[i], NT);
       bar_init(&fempty[i], kSymCompWarps);
-      bar_init(&gfull[i], 2);
+      bar_init(&gfull[i], NT);
       bar_init(&gfree[i], kSymCompWarps);
     }
     bar_init(qfull, 1);
     for (int i = 0; i < 4; ++i) bar_init(&fin[i], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) tmem_alloc(&tmem_slot, 512);
+  if (warp == 0) tmem_alloc(&tmem_slot, kCols);
   fence_before();
   __syncthreads();
   fence_after();
@@ -837,9 +843,9 @@ __global__ void __launch_bounds__(kSymGThreads, 1) k_near_sym_gtc(SymGArgs a) {
     if (lane == 0) {
       bool bad = false;
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      bar_expect_tx(qfull, static_cast<uint32_t>(ld * 64 + kXBytesLeaf256));
+      bar_expect_tx(qfull, static_cast<uint32_t>(ld * 64 + xbytes));
       bulk_load(qT, a.bq + static_cast<int64_t>(T) * ld * 32, static_cast<uint32_t>(ld * 64), qfull);
-      bulk_load(xT, a.xa + static_cast<int64_t>(T) * ld * kKD * 2, kXBytesLeaf256, qfull);
+      bulk_load(xT, a.xa + static_cast<int64_t>(T) * ld * kKD * 2, xbytes, qfull);
       int i = 0;
       for (int e = 0; e < ne && !bad; ++e) {
         const int S = a.ups[e0 + e];
@@ -893,7 +899,7 @@ __global__ void __launch_bounds__(kSymGThreads, 1) k_near_sym_gtc(SymGArgs a) {
             fence_after();
             const u64 ta = dT_a + ((eb * ebytes) >> 4);
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
+            for (int h = 0; h < NT; ++h) {
               const uint32_t dcol = tmem + (h == 0 ? kTr : kTr1) + static_cast<uint32_t>(tb * 32);
 #pragma unroll
               for (int jj = 0; jj < 8; ++jj) {
@@ -915,10 +921,10 @@ __global__ void __launch_bounds__(kSymGThreads, 1) k_near_sym_gtc(SymGArgs a) {
     // ---- G / forward issuers, one per target tile: G of chunk i + 2 ahead
     // of the forward products of chunk i
     const int at = warp == kSymCompWarps ? 0 : 1;
-    if (lane == 0) {
+    if (lane == 0 && at < NT) {
       bool bad = !wait_sleep(qfull, 0u);
       const uint32_t ebase = sptr(ebuf), sbase = sptr(stages), xtb = sptr(xT);
-      constexpr uint32_t xlo = 256 * kKD * 2;            // hi -> lo in the target block (bytes)
+      constexpr uint32_t xlo = ld * kKD * 2;             // hi -> lo in the target block (bytes)
       // G MMAs of chunk i (stage i % kStages) into G buffer i & 1
       // descriptors: the start address is the low field (address / 16), so a
       // byte offset o moves a descriptor by o / 16
@@ -934,7 +940,7 @@ __global__ void __launch_bounds__(kSymGThreads, 1) k_near_sym_gtc(SymGArgs a) {
         const u64 bhi = dG_b + ((st * stage_bytes) >> 4), blo = bhi + (kXChunkHalf >> 4);
         {
           const u64 ahi = dG_a + ((at * 16 * 256) >> 4), alo = ahi + (xlo >> 4);
-          const uint32_t d = tmem + kG + static_cast<uint32_t>(gb * 128 + at * 64);
+          const uint32_t d = tmem + kG + static_cast<uint32_t>(gb * kGB + at * 64);
           mma_f16(d, ahi, blo, kIdG, 0u);                // small terms first,
           mma_f16(d, alo, bhi, kIdG, 1u);
           mma_f16(d, ahi, bhi, kIdG, 1u);                // the large one last
@@ -965,7 +971,7 @@ __global__ void __launch_bounds__(kSymGThreads, 1) k_near_sym_gtc(SymGArgs a) {
           const u64 fa = dF_a + ((eb * ebytes) >> 4);
           const u64 fb_desc = dF_b + ((st * stage_bytes) >> 4);
           {
-            const uint32_t dcol = tmem + kF + static_cast<uint32_t>(fb * 64 + at * 32);
+            const uint32_t dcol = tmem + kF + static_cast<uint32_t>(fb * kFB + at * 32);
 #pragma unroll
             for (int kk = 0; kk < kChunk / 16; ++kk) {
               const u64 ahi = fa + ((at * 16 * kTS + kk * 2 * 128) >> 4);
@@ -984,9 +990,14 @@ __global__ void __launch_bounds__(kSymGThreads, 1) k_near_sym_gtc(SymGArgs a) {
       if (bad) atomicExch(a.err, 3);
     }
   } else {
-    // ---- compute warps: (quadrant qd, part p): target tile p / 2, sources 32 (p % 2) .. + 31 of each chunk
+    // ---- compute warps: (quadrant qd, part p): NT = 2: target tile p / 2,
+    // sources 32 (p % 2) .. + 31 of each chunk and right-hand sides 8 (p % 2)
+    // .. + 7 of the forward sums; NT = 1: sources 16 p .. + 15, right-hand
+    // sides 8 p .. + 7 for p < 2
     const int qd = warp & 3, part = warp >> 2;
-    const int at = part >> 1, sh = part & 1;
+    const int at = NT == 2 ? part >> 1 : 0, sh = NT == 2 ? part & 1 : part;
+    constexpr int kSrc = NT == 2 ? 32 : 16;   // sources per warp and chunk
+    const bool fown = NT == 2 || part < 2;
     const int tl = qd * 32 + lane;                 // target within the tile (TMEM lane)
     const int tt = at * 128 + tl;                  // target within T
     const uint32_t lane_base = tmem + (static_cast<uint32_t>(qd * 32) << 16);
@@ -1004,15 +1015,17 @@ __global__ void __launch_bounds__(kSymGThreads, 1) k_near_sym_gtc(SymGArgs a) {
         return;
       }
       fence_after();
-      uint32_t dv[8], dl[8];
-      const uint32_t col = lane_base + kF + static_cast<uint32_t>(fb * 64 + at * 32 + 8 * sh);
-      tmem_ld8x2(col, col + 16, dv, dl);
+      if (fown) {
+        uint32_t dv[8], dl[8];
+        const uint32_t col = lane_base + kF + static_cast<uint32_t>(fb * kFB + at * 32 + 8 * sh);
+        tmem_ld8x2(col, col + 16, dv, dl);
 #pragma unroll
-      for (int r = 0; r < 8; ++r) {
-        const float y = (__uint_as_float(dv[r]) + __uint_as_float(dl[r]) * kLoInv) - kc[r];
-        const float s = ks[r] + y;
-        kc[r] = (s - ks[r]) - y;
-        ks[r] = s;
+        for (int r = 0; r < 8; ++r) {
+          const float y = (__uint_as_float(dv[r]) + __uint_as_float(dl[r]) * kLoInv) - kc[r];
+          const float s = ks[r] + y;
+          kc[r] = (s - ks[r]) - y;
+          ks[r] = s;
+        }
       }
       fence_before();
       __syncwarp();
@@ -1028,13 +1041,16 @@ __global__ void __launch_bounds__(kSymGThreads, 1) k_near_sym_gtc(SymGArgs a) {
       fence_after();
       const int r0 = 4 * part;
       const uint32_t col = lane_base + kTr + static_cast<uint32_t>(tb * 32 + r0);
-      uint32_t x[4], y[4], x1[4], y1[4];
+      uint32_t x[4], y[4];
       tmem_ld4x2(col, col + 16, x, y);
-      tmem_ld4x2(col + (kTr1 - kTr), col + (kTr1 - kTr) + 16, x1, y1);   // the other K half
+      if (NT == 2) {
+        uint32_t x1[4], y1[4];
+        tmem_ld4x2(col + (kTr1 - kTr), col + (kTr1 - kTr) + 16, x1, y1);   // the other K half
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        x[j] = __float_as_uint(__uint_as_float(x[j]) + __uint_as_float(x1[j]));
-        y[j] = __float_as_uint(__uint_as_float(y[j]) + __uint_as_float(y1[j]));
+        for (int j = 0; j < 4; ++j) {
+          x[j] = __float_as_uint(__uint_as_float(x[j]) + __uint_as_float(x1[j]));
+          y[j] = __float_as_uint(__uint_as_float(y[j]) + __uint_as_float(y1[j]));
+        }
       }
       float* cb = comb + tb * (64 * 16);
       if (qd >= 2) {
@@ -1083,15 +1099,15 @@ __global__ void __launch_bounds__(kSymGThreads, 1) k_near_sym_gtc(SymGArgs a) {
           break;
         }
         fence_after();
-        // G in two halves: the second half's load is in flight while the
-        // first half is evaluated
+        // G in two halves (NT = 2): the second half's load is in flight
+        // while the first half is evaluated
         uint32_t g[32];
-        const uint32_t gaddr = lane_base + kG + static_cast<uint32_t>(gb * 128 + at * 64 + 32 * sh);
+        const uint32_t gaddr = lane_base + kG + static_cast<uint32_t>(gb * kGB + at * 64 + kSrc * sh);
         tmem_ld16(gaddr, g);
-        tmem_ld16_async(gaddr + 16, g + 16);
+        if (NT == 2) tmem_ld16_async(gaddr + 16, g + 16);
         const bool oke = i < 2 || wait_sleep(&efree[eb], static_cast<uint32_t>(((i - 2) >> 1) & 1));
         const uint32_t et = sptr(ebuf + eb * ebytes) +
-                            static_cast<uint32_t>((tt >> 3) * kTS + (tt & 7) * 16 + (4 * sh) * 128);
+                            static_cast<uint32_t>((tt >> 3) * kTS + (tt & 7) * 16 + (kSrc / 8 * sh) * 128);
         if (__all_sync(0xffffffffu, oke)) {
 #pragma unroll
           for (int q8 = 0; q8 < 2; ++q8) {
@@ -1104,7 +1120,7 @@ __global__ void __launch_bounds__(kSymGThreads, 1) k_near_sym_gtc(SymGArgs a) {
             sts128(et + q8 * 128 + kHL, lo);
           }
         }
-        tmem_wait_ld16(g + 16);
+        if (NT == 2) tmem_wait_ld16(g + 16);
         fence_before();
         __syncwarp();
         if (lane == 0) bar_arrive(&gfree[gb]);
@@ -1113,7 +1129,7 @@ __global__ void __launch_bounds__(kSymGThreads, 1) k_near_sym_gtc(SymGArgs a) {
           break;
         }
 #pragma unroll
-        for (int q8 = 2; q8 < 4; ++q8) {
+        for (int q8 = 2; q8 < kSrc / 8; ++q8) {
           uint32_t hi[4], lo[4];
 #pragma unroll
           for (int u = 0; u < 4; ++u)
@@ -1145,19 +1161,22 @@ __global__ void __launch_bounds__(kSymGThreads, 1) k_near_sym_gtc(SymGArgs a) {
     if (!bad && pend_jt >= 0) flush(pend_jt, pend_S, pend_c);
     if (!bad && ne >= 1) fold(ne - 1);
     if (bad && lane == 0) atomicExch(a.err, 3);
-    float* op = a.fwd + static_cast<int64_t>(T) * 16 * ld + tt;
+    if (fown) {
+      float* op = a.fwd + static_cast<int64_t>(T) * 16 * ld + tt;
 #pragma unroll
-    for (int r = 0; r < 8; ++r) op[(8 * sh + r) * ld] = ks[r];
+      for (int r = 0; r < 8; ++r) op[(8 * sh + r) * ld] = ks[r];
+    }
   }
   fence_before();
   __syncthreads();
   fence_after();
-  if (warp == 0) tmem_dealloc(tmem, 512);
+  if (warp == 0) tmem_dealloc(tmem, kCols);
 }
 
-size_t sym_g_smem() {
-  return 2 * static_cast<size_t>(2 * 16 * kTS) + kStages * static_cast<size_t>(2 * kXChunkHalf + kQChunkBytes) +
-         256 * 64 + kXBytesLeaf256 + 2 * 64 * 16 * 4;
+size_t sym_g_smem(int NT) {
+  const size_t ld = 128 * static_cast<size_t>(NT);
+  return 2 * static_cast<size_t>(NT * 16 * kTS) + kStages * static_cast<size_t>(2 * kXChunkHalf + kQChunkBytes) +
+         ld * 64 + ld * kKD * 2 * 2 + 2 * 64 * 16 * 4;
 }
 
 size_t sym_smem(int D, int ld) {
@@ -1190,7 +1209,7 @@ constexpr int kSymSmemMax = 220 * 1024;
 // The exponent on the tensor cores: Gaussian in factored form, leaves of 256
 // slots, padded dimension <= 16.
 bool sym_g_applies(const Plan& P, int D) {
-  return P.kernel == DWFMM_K_GAUSS && P.m_pad == 256 && D <= kKD && sym_g_smem() <= static_cast<size_t>(kSymSmemMax);
+  return P.kernel == DWFMM_K_GAUSS && P.m_pad == 256 && D <= kKD && sym_g_smem(2) <= static_cast<size_t>(kSymSmemMax);
 }
 
 }  // namespace
@@ -1238,7 +1257,8 @@ void ensure_sym_attrs() {
   sym_attrs_d<12>(kSymSmemMax);
   sym_attrs_d<16>(kSymSmemMax);
   sym_attrs_d<20>(kSymSmemMax);
-  cudaFuncSetAttribute(k_near_sym_gtc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSymSmemMax);
+  cudaFuncSetAttribute(k_near_sym_gtc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSymSmemMax);
+  cudaFuncSetAttribute(k_near_sym_gtc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSymSmemMax);
   DW_CUDA(cudaGetLastError());
   g_sym_attrs_dev.fetch_or(dbit);
 }
@@ -1306,7 +1326,7 @@ bool near_sym_tc(Plan& P, int D, int Rc, cudaStream_t s) {
     g.acc_scale = std::ldexp(1.0f, sb);
     g.ld = ld;
     g.err = P.d_err.p;
-    k_near_sym_gtc<<<P.L, kSymGThreads, sym_g_smem(), s>>>(g);
+    k_near_sym_gtc<2><<<P.L, kSymGThreads, sym_g_smem(2), s>>>(g);
     DW_CUDA(cudaGetLastError());
     k_sym_finish<<<ceil_div(nsite, 256), 256, 0, s>>>(P.sym_fwd.p, P.sym_acc.p, std::ldexp(1.0, -sb), P.d_ptsk.p,
                                                        gstride, P.L, ld, D, gauss, Rc, P.sym_colmax.p, P.ynear32.p,
@@ -1360,6 +1380,7 @@ bool m2l_sym_tc(Plan& P, int D, int Rc, cudaStream_t s) {
     k_m2l_crd<<<ceil_div(static_cast<int64_t>(C) * gstride, 256), 256, 0, s>>>(P.d_ynodek.p, C, D, np,
                                                                              P.m2l_crd.p);
     P.m2l_crd_D = D;
+    P.m2l_x16_D = -1;
   }
   P.m2l_bq16.alloc(static_cast<size_t>(C) * ld * 32);
   P.m2l_acc.alloc(static_cast<size_t>(nslot));
@@ -1380,19 +1401,43 @@ bool m2l_sym_tc(Plan& P, int D, int Rc, cudaStream_t s) {
   // fixed-point bits: a partial sum is at most (all nodes) x E'max x max |q'|
   const double emax = gauss ? std::exp2(2.0 * P.gauss_bound) : 1.0;
   const int sb = 62 - static_cast<int>(std::ceil(std::log2(static_cast<double>(C) * ld * emax * 2.0)));
-  SymArgs a{};
-  a.pts = P.m2l_crd.p;
-  a.gstride = gstride;
-  a.bq = P.m2l_bq16.p;
-  a.uprow = P.fsym_uprow.p;
-  a.ups = P.fsym_s.p;
-  a.order = P.fsym_order.p;
-  a.fwd = P.m2l_fwd.p;
-  a.acc = P.m2l_acc.p;
-  a.acc_scale = std::ldexp(1.0f, sb);
-  a.ld = ld;
-  a.err = P.d_err.p;
-  launch_sym_tc(D, P.kernel, a, P.fsym_rows, sym_smem(D, ld), s);
+  if (gauss && D <= kKD && sym_g_smem(1) <= static_cast<size_t>(kSymSmemMax)) {
+    // the Gaussian's exponent on the tensor cores, one 128-target tile
+    if (P.m2l_x16_D != D || !P.m2l_xa16.p) {
+      P.m2l_xa16.alloc(static_cast<size_t>(C) * ld * kKD * 2);
+      P.m2l_xb16.alloc(static_cast<size_t>(C) * ld * kKD * 2);
+      k_sym_make_x16<<<ceil_div(static_cast<int64_t>(C) * ld * kKD, 256), 256, 0, s>>>(
+          P.m2l_crd.p, gstride, C, ld, D, P.m2l_xa16.p, P.m2l_xb16.p);
+      P.m2l_x16_D = D;
+    }
+    SymGArgs g{};
+    g.xa = P.m2l_xa16.p;
+    g.xb = P.m2l_xb16.p;
+    g.bq = P.m2l_bq16.p;
+    g.uprow = P.fsym_uprow.p;
+    g.ups = P.fsym_s.p;
+    g.order = P.fsym_order.p;
+    g.fwd = P.m2l_fwd.p;
+    g.acc = P.m2l_acc.p;
+    g.acc_scale = std::ldexp(1.0f, sb);
+    g.ld = ld;
+    g.err = P.d_err.p;
+    k_near_sym_gtc<1><<<P.fsym_rows, kSymGThreads, sym_g_smem(1), s>>>(g);
+  } else {
+    SymArgs a{};
+    a.pts = P.m2l_crd.p;
+    a.gstride = gstride;
+    a.bq = P.m2l_bq16.p;
+    a.uprow = P.fsym_uprow.p;
+    a.ups = P.fsym_s.p;
+    a.order = P.fsym_order.p;
+    a.fwd = P.m2l_fwd.p;
+    a.acc = P.m2l_acc.p;
+    a.acc_scale = std::ldexp(1.0f, sb);
+    a.ld = ld;
+    a.err = P.d_err.p;
+    launch_sym_tc(D, P.kernel, a, P.fsym_rows, sym_smem(D, ld), s);
+  }
   DW_CUDA(cudaGetLastError());
   const int64_t off = static_cast<int64_t>(first) * 16 * ld;
   k_sym_finish<<<ceil_div(static_cast<int64_t>(nc) * 16 * ld, 256), 256, 0, s>>>(
