@@ -430,6 +430,7 @@ def run_ours(args):
     t0 = time.perf_counter()
     plan = Plan(d=d, kernel=w.kernel, sigma=w.sigma, gamma=w.gamma, q=w.q, eta=w.eta,
                 leaf_size=w.leaf, precision=args.precision, max_rhs=R)
+    plan.set_m2l_engine(args.m2l_engine)
     setup_ms = (time.perf_counter() - t0) * 1e3
     Xd = torch.from_numpy(X).to(dev)
     torch.cuda.synchronize()
@@ -943,6 +944,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="mixed", choices=["mixed", "fp64", "small"])
     ap.add_argument("--precision", default="mixed", choices=["fp64", "fp32", "mixed"])
+    ap.add_argument("--m2l-engine", default="auto",
+                    choices=["auto", "mixed_tf32_tensor", "mixed_symmetric_fp16_tensor"],
+                    help="M2L engine of the mixed matvec (auto: timed once per tree)")
     ap.add_argument("--cpu-steps", type=int, default=2)
     ap.add_argument("--n", type=int, default=0, help="override N (smaller case for profiling)")
     ap.add_argument("--no-solve", action="store_true")
