@@ -730,7 +730,15 @@ constexpr int kKD = 16;                                  // padded dimension of 
 constexpr uint32_t kIdG = idesc_f16(128, 64, 0);
 constexpr int kXChunkHalf = (kChunk / 8) * (kKD / 8) * 128;   // 2 KB: one of hi / lo of a chunk
 
-// hi / lo FP16 coordinate blocks: xa = 2x' (target role), xb = x' (source role)
+// hi / lo FP16 coordinate blocks: xa = 2x' (target role), xb = x' (source role).
+// hi = the coordinate rounded to FP16, lo = the exact FP32 remainder rounded
+// to FP16: |lo| <= 2^-11 |v| with either sign, so the lo * lo product the G
+// contraction leaves out is <= 2^-22 of a term and unbiased.  (Truncating hi
+// instead leaves a remainder of up to 2^-10 |v| with the sign of v: the
+// dropped lo * lo terms then all shrink |G| and bias E' = 2^G by up to
+// 2^-20 |G| relative, a smooth error that does not average out in K x.)
+// Remainders of coordinates below 2^-3 are FP16 subnormals: absolute error
+// <= 2^-25, far below the accumulator's rounding of G.
 __global__ void k_sym_make_x16(const float* pts, int64_t gstride, int L, int ld, int D, uint16_t* xa, uint16_t* xb) {
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= static_cast<int64_t>(L) * ld * kKD) return;
@@ -739,9 +747,10 @@ __global__ void k_sym_make_x16(const float* pts, int64_t gstride, int L, int ld,
   const int p = static_cast<int>(gp % ld);
   const int64_t g = gp / ld;
   const float v = k < D ? pts[g * gstride + static_cast<int64_t>(k) * ld + p] : 0.0f;
-  const float h = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
-  const __half hh = __float2half_rn(h), hl = __float2half_rn(v - h);
-  const __half ah = __float2half_rn(2.0f * h), al = __float2half_rn(2.0f * (v - h));
+  const __half hh = __float2half_rn(v);
+  const float r = v - __half2float(hh);                                   // exact
+  const __half hl = __float2half_rn(r);
+  const __half ah = __float2half_rn(2.0f * __half2float(hh)), al = __float2half_rn(2.0f * r);
   const int64_t blk = g * static_cast<int64_t>(ld) * kKD * 2;            // halfs per leaf
   const int64_t off = (p / 8) * (kKD / 8) * 64 + (k / 8) * 64 + (p % 8) * 8 + (k % 8);
   const int64_t lo = static_cast<int64_t>(ld) * kKD;                      // hi -> lo
