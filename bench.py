@@ -797,8 +797,9 @@ def run_cfg2_solve(args):
 def run_batch(args):
     """The batching workload: 256 independent problems (N log-uniform in
     [2048, 65536], d in {6..12}, gamma_k = k^-2, Matern-3/2, q = 5, 1-8
-    right-hand sides, float32) as one fused batch matvec under a captured
-    graph, against the same problems' matvecs one after another.  Throughput
+    right-hand sides, float32) as one fused batch matvec (the engine chosen at
+    creation: captured launches or one persistent launch; both are timed),
+    against the same problems' matvecs one after another.  Throughput
     is sum_p N_p R_p per second; L2 flushed between steps."""
     import torch
     import __graft_entry__ as ge
@@ -843,6 +844,13 @@ def run_batch(args):
             out.append(a.elapsed_time(z))
         return statistics.mean(out)
 
+    eng = b.engine()
+    ms_engine = {}
+    engines = ["graph", "persistent"] if eng["persistent_available"] else ["graph"]
+    for e in engines:
+        b.set_engine(e)
+        ms_engine[e] = timed(lambda: b.matvec(xs, ys), args.steps)
+    b.set_engine(eng["engine"])
     ms_batch = timed(lambda: b.matvec(xs, ys), args.steps)
 
     def one_by_one():
@@ -863,6 +871,8 @@ def run_batch(args):
                + ("one launch per right-hand-side class" if info[k]["per_class"] else "one padded launch")
             for k in ("near_shape", "m2l_shape")},
         "autotune_ms": info["tune_ms"], "leaves": info["leaves"],
+        "engine": eng["engine"], "engine_ms": ms_engine, "engine_tune_ms": eng["ms"],
+        "persistent_launch": eng["persistent_launch"],
         "l2": "flushed between steps (512 MiB write)"}), flush=True)
     b.close()
     for p in plans:

@@ -284,6 +284,33 @@ dwfmm_status dwfmm_batch_info(dwfmm_batch batch, int32_t* split, double* tune_ms
  * Errors: INVALID_ARG (NULL batch or shape).  No counterpart in the paper. */
 dwfmm_status dwfmm_batch_shape(dwfmm_batch batch, int32_t* shape);
 
+/* Engines of a batch matvec.  0: the captured graph of launches described at
+ * dwfmm_batch_create.  1: one persistent cooperative launch for the whole
+ * matvec (every CTA resident; the phases separated by grid-wide barriers
+ * whose waits are bounded: a wait that gives up ends the launch early and
+ * raises the batch's device error flag instead of hanging; at creation that
+ * makes the engine unavailable).  In it, CTAs that have finished their
+ * share of a far-field phase (the upward pass by height, the couplings from
+ * a work queue, the downward pass by level) take near-field target groups
+ * from a second work queue while they wait, and all right-hand-side classes
+ * share the queues; near-field and coupling target groups run on groups of
+ * 32, 64 or 128 threads of a CTA.  Both engines sum every target in the same
+ * order: their results are equal bit for bit.  At creation the persistent
+ * engine is timed at every near-field group width against the graph, and the
+ * faster engine is used (if the device can launch it and a stream capture
+ * holds it).
+ * dwfmm_batch_engine: engine[0] the engine in use, engine[1] 1 if the
+ *   persistent engine is available; ms[0], ms[1] the best timed matvec of
+ *   each engine at creation (-1 if not timed); launch[0..2] the persistent
+ *   launch's CTAs and the near-field and coupling group widths (0 if not
+ *   available).  Host arrays of 2, 2 and 3 elements.
+ * dwfmm_batch_set_engine: selects engine 0 or 1 for later matvecs and
+ *   batched CG steps; DWFMM_ERR_STATE if 1 is not available.
+ * Errors: INVALID_ARG (NULL batch or output, engine outside 0..1).  No
+ * counterpart in the paper (a scheduling choice). */
+dwfmm_status dwfmm_batch_engine(dwfmm_batch batch, int32_t* engine, double* ms, int32_t* launch);
+dwfmm_status dwfmm_batch_set_engine(dwfmm_batch batch, int32_t engine);
+
 /* Batched CG (Sec. 2, Eq. (2.2); the CG of Sec. 6.2): `iters` iterations of
  * the incremental CG of every problem of the batch, each begun with
  * dwfmm_cg_begin on its plan (its own lambda, right-hand sides and rtol,

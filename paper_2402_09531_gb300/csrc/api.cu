@@ -789,6 +789,20 @@ dwfmm_status dwfmm_batch_shape(dwfmm_batch batch, int32_t* shape) {
   return DWFMM_OK;
 }
 
+dwfmm_status dwfmm_batch_engine(dwfmm_batch batch, int32_t* engine, double* ms, int32_t* launch) {
+  if (!batch || !engine || !ms || !launch) return DWFMM_ERR_INVALID_ARG;
+  dw::batch_engine(*batch->B, engine, ms, launch);
+  return DWFMM_OK;
+}
+
+dwfmm_status dwfmm_batch_set_engine(dwfmm_batch batch, int32_t engine) {
+  if (!batch || engine < 0 || engine > 1) return DWFMM_ERR_INVALID_ARG;
+  return guarded(nullptr, [&]() -> dwfmm_status {
+    dw::batch_set_engine(*batch->B, engine);
+    return DWFMM_OK;
+  });
+}
+
 dwfmm_status dwfmm_batch_destroy(dwfmm_batch batch) {
   if (!batch) return DWFMM_OK;
   dw::batch_delete(batch->B);

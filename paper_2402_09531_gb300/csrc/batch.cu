@@ -62,6 +62,16 @@ struct Batch {
   int cg_iters = -1, cg_nseg = -1, cg_nblk = -1;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  // persistent engine: the whole matvec as one cooperative launch
+  bool persist_ok = false;       // eligible (launch and capture worked, no wait gave up)
+  bool persistent = false;       // the engine in use
+  PersistArgs pa{};
+  int pgrid = 0;
+  size_t psmem = 0;
+  DBuf<unsigned> psync;
+  double engine_ms[2] = {-1.0, -1.0};   // best timed matvec: launches in a graph, persistent
+  cudaGraph_t pgraph = nullptr;
+  cudaGraphExec_t pexec = nullptr;
 
   void release() {
     if (cg_exec) cudaGraphExecDestroy(cg_exec);
@@ -75,6 +85,10 @@ struct Batch {
     cg_ev = nullptr;
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
+    if (pexec) cudaGraphExecDestroy(pexec);
+    if (pgraph) cudaGraphDestroy(pgraph);
+    pexec = nullptr;
+    pgraph = nullptr;
     if (h_probs) cudaFreeHost(h_probs);
     if (ev_fork) cudaEventDestroy(ev_fork);
     if (ev_join) cudaEventDestroy(ev_join);
@@ -170,9 +184,23 @@ void enqueue_m2l(Batch& B, bool split, int threads, cudaStream_t s) {
   }
 }
 
-void enqueue_matvec(Batch& B) {
+// io = false leaves out the gather of the callers' x and the scatter to their
+// y (for timing at creation, before any caller buffer is known).
+cudaError_t enqueue_persistent(Batch& B, cudaStream_t s, bool io) {
+  const cudaError_t e = cudaMemsetAsync(B.psync.p, 0, sizeof(unsigned) * kPersistSync, s);
+  if (e != cudaSuccess) return e;
+  PersistArgs a = B.pa;
+  a.io = io ? 1 : 0;
+  return launch_batch_persistent(B.D, B.kernel, a, B.pgrid, B.psmem, s);
+}
+
+void enqueue_matvec(Batch& B, bool io = true) {
+  if (B.persistent) {
+    DW_CUDA(enqueue_persistent(B, B.stream, io));
+    return;
+  }
   cudaStream_t s = B.stream;
-  launch_gather_batched(B.probs.p, B.d_leaf_off.p, B.P, B.Ltot, B.ld, B.xb.p, s);
+  if (io) launch_gather_batched(B.probs.p, B.d_leaf_off.p, B.P, B.Ltot, B.ld, B.xb.p, s);
   DW_CUDA(cudaEventRecord(B.ev_fork, s));
   DW_CUDA(cudaStreamWaitEvent(B.side, B.ev_fork, 0));
   enqueue_near(B, B.split, B.thr_near, B.side);
@@ -183,7 +211,7 @@ void enqueue_matvec(Batch& B) {
   for (size_t j = 0; j < B.down_off.size(); ++j)
     launch_downward_batched(B.probs.p, B.work.p + B.down_off[j], B.down_cnt[j], B.far_smem, s);
   DW_CUDA(cudaStreamWaitEvent(s, B.ev_join, 0));
-  launch_scatter_batched(B.probs.p, B.d_leaf_off.p, B.P, B.Ltot, B.ld, B.ynear.p, B.yfar.p, s);
+  if (io) launch_scatter_batched(B.probs.p, B.d_leaf_off.p, B.P, B.Ltot, B.ld, B.ynear.p, B.yfar.p, s);
   DW_CUDA(cudaGetLastError());
 }
 
@@ -247,6 +275,187 @@ void tune_shapes(Batch& B) {
   }
   B.tune_ms[0] = best_pad;
   B.tune_ms[1] = best_split;
+}
+
+// --- persistent engine -------------------------------------------------------
+
+int pow2_width(int t) { return t <= 32 ? 32 : t <= 64 ? 64 : 128; }
+
+// Arguments of the persistent kernel with near-field groups of gs_near threads
+// and coupling groups of gs_m2l; its shared memory and grid (every CTA
+// resident).  False if the batch does not fit the kernel's tables or an SM.
+bool build_persist_args(Batch& B, int gs_near, int gs_m2l) {
+  if (B.up_off.size() > static_cast<size_t>(kPersistMaxLev) ||
+      B.down_off.size() > static_cast<size_t>(kPersistMaxLev) ||
+      B.classes.size() > static_cast<size_t>(kPersistMaxSeg))
+    return false;
+  PersistArgs& a = B.pa;
+  a = PersistArgs{};
+  a.probs = B.probs.p;
+  a.leaf_off = B.d_leaf_off.p;
+  a.work = B.work.p;
+  a.P = B.P;
+  a.Ltot = B.Ltot;
+  a.ld = B.ld;
+  a.xb = B.xb.p;
+  a.ynear = B.ynear.p;
+  a.yfar = B.yfar.p;
+  a.nup = static_cast<int>(B.up_off.size());
+  a.ndown = static_cast<int>(B.down_off.size());
+  for (int h = 0; h < a.nup; ++h) {
+    a.up_off[h] = B.up_off[h];
+    a.up_cnt[h] = B.up_cnt[h];
+  }
+  for (int j = 0; j < a.ndown; ++j) {
+    a.down_off[j] = B.down_off[j];
+    a.down_cnt[j] = B.down_cnt[j];
+  }
+  int rcn = 1, rcm = 1;
+  // the largest right-hand-side class first: the longest items leave the queue first
+  for (auto it = B.classes.rbegin(); it != B.classes.rend(); ++it) {
+    const Batch::Cls& c = *it;
+    if (c.leaf_count > 0) {
+      PersistSeg& sg = a.near[a.nnear++];
+      sg.a = p2p_args(B, c.RC, c.leaf_first);
+      sg.rc = c.RC;
+      sg.count = c.leaf_count;
+      sg.ilv_src = B.xb.p;
+      a.near_total += c.leaf_count;
+      rcn = std::max(rcn, c.RC);
+    }
+    if (c.clus_count > 0) {
+      PersistSeg& sg = a.m2l[a.nm2l++];
+      sg.a = m2l_args(B, c.RC, c.clus_first);
+      sg.rc = c.RC;
+      sg.count = c.clus_count;
+      sg.ilv_src = B.mom.p;
+      a.m2l_total += c.clus_count;
+      rcm = std::max(rcm, c.RC);
+    }
+  }
+  a.gs_near = gs_near;
+  a.gs_m2l = gs_m2l;
+  const size_t gn = persist_group_bytes(B.D, rcn, B.ld, gs_near), gm = persist_group_bytes(B.D, rcm, B.n_pad, gs_m2l);
+  a.near_group_bytes = static_cast<int>(gn);
+  a.m2l_group_bytes = static_cast<int>(gm);
+  a.sync = B.psync.p;
+  a.err = B.err.p;
+  B.psmem = std::max({B.far_smem, static_cast<size_t>(kPersistThreads / gs_near) * gn,
+                      static_cast<size_t>(kPersistThreads / gs_m2l) * gm});
+  if (B.psmem > 227 * 1024) return false;
+  const int per_sm = persist_blocks_per_sm(B.D, B.kernel, B.psmem);
+  if (per_sm < 1) return false;
+  B.pgrid = per_sm * sm_count();
+  return true;
+}
+
+// One matvec of either engine captured on the batch's stream (graph and
+// executable); false if the capture or the instantiation is refused.
+bool capture_engine(Batch& B, bool persistent, bool io, cudaGraph_t* graph, cudaGraphExec_t* exec) {
+  *graph = nullptr;
+  *exec = nullptr;
+  if (cudaStreamBeginCapture(B.stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  const bool keep = B.persistent;
+  B.persistent = persistent;
+  cudaError_t le = cudaSuccess;
+  if (persistent) le = enqueue_persistent(B, B.stream, io);
+  else enqueue_matvec(B, io);
+  B.persistent = keep;
+  cudaGraph_t g = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(B.stream, &g);
+  if (le != cudaSuccess || ce != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    (void)cudaGetLastError();
+    return false;
+  }
+  cudaGraphExec_t e = nullptr;
+  if (cudaGraphInstantiate(&e, g, 0) != cudaSuccess) {
+    cudaGraphDestroy(g);
+    (void)cudaGetLastError();
+    return false;
+  }
+  *graph = g;
+  *exec = e;
+  return true;
+}
+
+void drop_graph(cudaGraph_t* g, cudaGraphExec_t* e) {
+  if (*e) cudaGraphExecDestroy(*e);
+  if (*g) cudaGraphDestroy(*g);
+  *e = nullptr;
+  *g = nullptr;
+}
+
+// Best of two timed replays of a captured matvec (after one untimed).
+double time_exec(Batch& B, cudaGraphExec_t e) {
+  cudaEvent_t a, b;
+  DW_CUDA(cudaEventCreate(&a));
+  DW_CUDA(cudaEventCreate(&b));
+  DW_CUDA(cudaGraphLaunch(e, B.stream));
+  float best = 1e30f;
+  for (int rep = 0; rep < 2; ++rep) {
+    DW_CUDA(cudaEventRecord(a, B.stream));
+    DW_CUDA(cudaGraphLaunch(e, B.stream));
+    DW_CUDA(cudaEventRecord(b, B.stream));
+    DW_CUDA(cudaEventSynchronize(b));
+    float ms = 0.f;
+    DW_CUDA(cudaEventElapsedTime(&ms, a, b));
+    best = std::min(best, ms);
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return best;
+}
+
+// Reads and clears the batch's error flag (a bounded device wait gave up).
+bool take_device_error(Batch& B) {
+  int e = 0;
+  DW_CUDA(cudaMemcpy(&e, B.err.p, sizeof(int), cudaMemcpyDeviceToHost));
+  if (e) DW_CUDA(cudaMemset(B.err.p, 0, sizeof(int)));
+  return e != 0;
+}
+
+// Times the persistent engine at each near-field group width (32, 64, 128
+// threads up to the widest the leaves use; the couplings keep the width the
+// launch tuner chose) against the captured launches, and keeps the faster.
+// Both are timed without the gather and the scatter (no caller buffers
+// exist yet; those two phases are the same elementwise work in both).
+void tune_persistent(Batch& B) {
+  B.persist_ok = false;
+  B.persistent = false;
+  int dev = 0, coop = 0;
+  DW_CUDA(cudaGetDevice(&dev));
+  DW_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t e = nullptr;
+  if (!capture_engine(B, false, false, &g, &e)) fail(DWFMM_ERR_CUDA, "capture of the batch matvec failed");
+  B.engine_ms[0] = time_exec(B, e);
+  drop_graph(&g, &e);
+  if (!coop) return;
+  B.psync.alloc(kPersistSync);
+  const int gs_m2l = pow2_width(B.thr_m2l);
+  const int widest = pow2_width(threads_for(B.ld));
+  double best = 1e30;
+  int best_gs = 0;
+  for (int gs = 32; gs <= widest; gs *= 2) {
+    if (!build_persist_args(B, gs, gs_m2l)) continue;
+    if (!capture_engine(B, true, false, &g, &e)) return;
+    const double ms = time_exec(B, e);
+    drop_graph(&g, &e);
+    if (take_device_error(B)) return;
+    if (ms < best) {
+      best = ms;
+      best_gs = gs;
+    }
+  }
+  if (!best_gs || !build_persist_args(B, best_gs, gs_m2l)) return;
+  if (!capture_engine(B, true, true, &B.pgraph, &B.pexec)) return;
+  B.persist_ok = true;
+  B.engine_ms[1] = best;
+  B.persistent = best < B.engine_ms[0];
 }
 
 }  // namespace
@@ -431,6 +640,8 @@ void batch_create(Batch& B, Plan* const* plans, const int32_t* nrhs, int count) 
   enqueue_matvec(B);
   DW_CUDA(cudaStreamEndCapture(B.stream, &B.graph));
   DW_CUDA(cudaGraphInstantiate(&B.exec, B.graph, 0));
+  // then the persistent engine against it
+  tune_persistent(B);
 }
 
 void batch_matvec(Batch& B, const double* const* x, double* const* y, cudaStream_t s) {
@@ -446,8 +657,29 @@ void batch_matvec(Batch& B, const double* const* x, double* const* y, cudaStream
   DW_CUDA(cudaMemcpyAsync(B.probs.p, B.h_probs, sizeof(ProbF32) * B.P, cudaMemcpyHostToDevice, s));
   DW_CUDA(cudaEventRecord(B.ev_copy, s));
   B.copied = true;
-  DW_CUDA(cudaGraphLaunch(B.exec, s));
+  DW_CUDA(cudaGraphLaunch(B.persistent ? B.pexec : B.exec, s));
   DW_CUDA(cudaGetLastError());
+}
+
+void batch_set_engine(Batch& B, int persistent) {
+  if (persistent && !B.persist_ok) fail(DWFMM_ERR_STATE, "the persistent engine is not available for this batch");
+  if (B.persistent == (persistent != 0)) return;
+  B.persistent = persistent != 0;
+  // captured CG iterations hold the other engine
+  if (B.cg_exec) cudaGraphExecDestroy(B.cg_exec);
+  if (B.cg_graph) cudaGraphDestroy(B.cg_graph);
+  B.cg_exec = nullptr;
+  B.cg_graph = nullptr;
+}
+
+void batch_engine(const Batch& B, int32_t* engine, double* ms, int32_t* launch) {
+  engine[0] = B.persistent ? 1 : 0;
+  engine[1] = B.persist_ok ? 1 : 0;
+  ms[0] = B.engine_ms[0];
+  ms[1] = B.engine_ms[1];
+  launch[0] = B.persist_ok ? B.pgrid : 0;
+  launch[1] = B.persist_ok ? B.pa.gs_near : 0;
+  launch[2] = B.persist_ok ? B.pa.gs_m2l : 0;
 }
 
 }  // namespace dw

@@ -143,6 +143,49 @@ struct SumArgs {
   int* err;
 };
 
+// The persistent batch matvec (one cooperative launch, farfield.cu): the
+// phases of the batch's fused matvec as work items of one kernel, separated
+// by grid-wide barriers with bounded waits.
+constexpr int kPersistThreads = 128;
+constexpr int kPersistMaxSeg = 4;     // right-hand-side classes
+constexpr int kPersistMaxLev = 32;    // tree heights / levels
+constexpr int kPersistSync = 2 * kPersistMaxLev + 8;   // barrier counters, then the two queue heads
+
+// One right-hand-side class of the near field or of the couplings: its
+// summation arguments (a.first = the class's first target group), padded
+// right-hand sides, and target-group count.  The class's charges are
+// interleaved first from the row layout of every group, ilv_src
+// [group][16][a.ld], into a.q ([group][a.ld][rc]), groups a.first ..
+// a.first + count - 1.
+struct PersistSeg {
+  SumArgs a;
+  int rc;
+  int count;
+  const float* ilv_src;
+};
+
+struct PersistArgs {
+  const ProbF32* probs;
+  const int* leaf_off;
+  const int2* work;           // upward items by height, then downward items by level
+  int P, Ltot, ld;
+  float* xb;                  // gathered right-hand sides [Ltot][16][ld]
+  const float* ynear;
+  const float* yfar;
+  int nup, ndown;
+  int up_off[kPersistMaxLev], up_cnt[kPersistMaxLev];
+  int down_off[kPersistMaxLev], down_cnt[kPersistMaxLev];
+  int nnear, nm2l;
+  PersistSeg near[kPersistMaxSeg], m2l[kPersistMaxSeg];
+  int near_total, m2l_total;
+  int gs_near, gs_m2l;                      // threads per target group (32, 64, 128)
+  int near_group_bytes, m2l_group_bytes;    // shared-memory stage bytes per group
+  unsigned* sync;             // [kPersistSync], zero at launch
+  int* err;
+  int io;                     // 1: gather the callers' x first and scatter to their y last
+};
+
+
 struct TreeDev {
   int64_t N;
   int J;
@@ -380,6 +423,12 @@ void launch_gather_batched(const ProbF32* probs, const int* leaf_off, int P, int
                            cudaStream_t s);
 void launch_scatter_batched(const ProbF32* probs, const int* leaf_off, int P, int Ltot, int ld, const float* ynear,
                             const float* yfar, cudaStream_t s);
+// persistent batch matvec: dynamic shared memory and resident CTAs per SM
+// for a launch, and the cooperative launch itself (false if the launch was
+// refused, e.g. by a stream capture that cannot hold it)
+size_t persist_group_bytes(int D, int RC, int ld, int threads);
+int persist_blocks_per_sm(int D, int kernel, size_t smem);
+cudaError_t launch_batch_persistent(int D, int kernel, const PersistArgs& pa, int grid, size_t smem, cudaStream_t s);
 int sum_padded_dim(int d);
 int sum_padded_rc(int r);
 size_t sum_stage_bytes(int D, int RC, int ld);
@@ -406,6 +455,8 @@ void batch_create(Batch& B, Plan* const* plans, const int32_t* nrhs, int count);
 void batch_matvec(Batch& B, const double* const* x, double* const* y, cudaStream_t s);
 void batch_info(const Batch& B, int32_t* split, double* tune_ms, int64_t* leaves);
 void batch_shape(const Batch& B, int32_t* shape);
+void batch_engine(const Batch& B, int32_t* engine, double* ms, int32_t* launch);
+void batch_set_engine(Batch& B, int persistent);
 dwfmm_status direct_sum_noalloc(int kernel, double sigma, const double* pts, int64_t n, int d, int64_t ldp,
                                 const double* x, double* y, int R, int64_t ldx, int64_t ldy,
                                 cudaStream_t s);

@@ -16,6 +16,7 @@
 #include <algorithm>
 
 #include "dwfmm_internal.cuh"
+#include "sum_f32.cuh"
 
 namespace dw {
 
@@ -283,9 +284,9 @@ __device__ __forceinline__ int problem_of(const int* leaf_off, int P, int gl) {
   return lo;
 }
 
-__global__ void k_gather_batched(const ProbF32* probs, const int* leaf_off, int P, int Ltot, int ld, float* xb) {
-  const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (t >= static_cast<int64_t>(Ltot) * kRC * ld) return;
+// Element t of the gathered right-hand sides xb[leaf][r][ld] (t < Ltot * 16 * ld).
+__device__ __forceinline__ void gather_elem(const ProbF32* probs, const int* leaf_off, int P, int ld, float* xb,
+                                            int64_t t) {
   const int i = static_cast<int>(t % ld);
   const int64_t lr = t / ld;
   const int r = static_cast<int>(lr % kRC);
@@ -298,10 +299,15 @@ __global__ void k_gather_batched(const ProbF32* probs, const int* leaf_off, int 
   xb[t] = v;
 }
 
-__global__ void k_scatter_batched(const ProbF32* probs, const int* leaf_off, int P, int Ltot, int ld,
-                                  const float* ynear, const float* yfar) {
+__global__ void k_gather_batched(const ProbF32* probs, const int* leaf_off, int P, int Ltot, int ld, float* xb) {
   const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t >= static_cast<int64_t>(Ltot) * kRC * ld) return;
+  gather_elem(probs, leaf_off, P, ld, xb, t);
+}
+
+// Element t of y = near + far, written to the caller's order (t < Ltot * 16 * ld).
+__device__ __forceinline__ void scatter_elem(const ProbF32* probs, const int* leaf_off, int P, int ld,
+                                             const float* ynear, const float* yfar, int64_t t) {
   const int i = static_cast<int>(t % ld);
   const int64_t lr = t / ld;
   const int r = static_cast<int>(lr % kRC);
@@ -313,6 +319,243 @@ __global__ void k_scatter_batched(const ProbF32* probs, const int* leaf_off, int
   double v = static_cast<double>(ynear[t]);
   if (p.jmin <= p.J) v += static_cast<double>(yfar[t]);
   p.y[static_cast<int64_t>(r) * p.ldy + p.perm[p.begin[c] + i]] = v;
+}
+
+__global__ void k_scatter_batched(const ProbF32* probs, const int* leaf_off, int P, int Ltot, int ld,
+                                  const float* ynear, const float* yfar) {
+  const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= static_cast<int64_t>(Ltot) * kRC * ld) return;
+  scatter_elem(probs, leaf_off, P, ld, ynear, yfar, t);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent batch matvec: the whole fused matvec of a batch as one
+// cooperative launch (every CTA resident at once).  Phases, each ended by a
+// grid-wide barrier (one arrival counter per phase, bounded wait):
+//   gather | interleave of the near-field charges, P2M of the leaves |
+//   M2M, one phase per height | interleave of the moments | the couplings
+//   (M2L, work queue) | L2L and L2P, one phase per level | the rest of the
+//   near field | scatter.
+// The near field (P2P) needs only the gathered charges, so from the second
+// barrier on a CTA that has done its share of a far-field phase takes
+// near-field target groups from a work queue while it waits for the others:
+// the short phases of the coarse levels no longer leave SMs idle, and all
+// right-hand-side classes share one queue (no tail per class).  Near-field
+// and coupling target groups run on groups of gs threads (several per CTA:
+// the tuned width), each group with its own stages and stage barriers,
+// taking items on its own until its queue is empty or its barrier completes;
+// the summation order inside a target group is that of k_sum_f32, so the
+// result equals the launch-per-phase matvec bit for bit.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// A barrier waits at most this long with nothing to do (every CTA is
+// resident, so the others only have their share of one phase left).
+constexpr uint64_t kPersistWaitNs = 4000000000ull;
+
+template <int D, int KER>
+__device__ __forceinline__ bool persist_sum_item(const PersistSeg* segs, int nseg, int idx, const sk::Grp& G,
+                                                 unsigned char* sm, uint64_t* full, int& tiles) {
+  int s = 0;
+  while (s + 1 < nseg && idx >= segs[s].count) {
+    idx -= segs[s].count;
+    ++s;
+  }
+  const PersistSeg& sg = segs[s];
+  const int g = sg.a.first + idx;
+  switch (sg.rc) {
+    case 1: return sk::sum_block<D, 1, KER>(sg.a, g, G, sm, full, tiles);
+    case 4: return sk::sum_block<D, 4, KER>(sg.a, g, G, sm, full, tiles);
+    case 8: return sk::sum_block<D, 8, KER>(sg.a, g, G, sm, full, tiles);
+    default: return sk::sum_block<D, 16, KER>(sg.a, g, G, sm, full, tiles);
+  }
+}
+
+// Shared state of a persistent CTA: stage barriers and completed-stage counts
+// of up to four groups, the item each group took, a broadcast word.
+struct PShared {
+  uint64_t full[kPersistThreads / 32][2];
+  int tiles[kPersistThreads / 32];
+  int item[kPersistThreads / 32];
+  int flag;
+};
+
+// Summation items from a queue (head `head`, `total` items): every group of
+// gs threads takes target groups one at a time and sums them, on its own,
+// until the queue is empty or, if `stop` is given, the barrier counter *stop
+// has reached gridDim.x (checked by the group's first thread between items).
+// 0: the queue is empty; 1: stopped by the barrier; -1: a copy wait gave up
+// (error flag set).
+template <int D, int KER>
+__device__ __noinline__ int persist_drain(const PersistSeg* segs, int nseg, int total, unsigned* head, int gs,
+                                          int gbytes, unsigned char* smem, PShared& sh, const unsigned* stop) {
+  const int gid = static_cast<int>(threadIdx.x) / gs;
+  const sk::Grp G{static_cast<int>(threadIdx.x) % gs, gs, 1 + gid};
+  unsigned char* gsm = smem + static_cast<size_t>(gid) * gbytes;
+  int tiles = sh.tiles[gid];
+  bool ok = true, empty = false;
+  for (;;) {
+    if (G.tid == 0) {
+      int it = -1;   // -1: the barrier is complete
+      if (!stop || ld_acquire_gpu(stop) < gridDim.x) it = static_cast<int>(atomicAdd(head, 1u));
+      sh.item[gid] = it;
+    }
+    sk::grp_sync(G);
+    const int it = sh.item[gid];
+    sk::grp_sync(G);   // read by every thread before the next item overwrites it
+    if (it < 0) break;
+    if (it >= total) {
+      empty = true;
+      break;
+    }
+    if (!persist_sum_item<D, KER>(segs, nseg, it, G, gsm, sh.full[gid], tiles)) {
+      ok = false;
+      break;
+    }
+  }
+  if (G.tid == 0) sh.tiles[gid] = tiles;
+  const int bad = __syncthreads_or(!ok);
+  const int emp = __syncthreads_or(empty);
+  return bad ? -1 : (emp ? 0 : 1);
+}
+
+// Arrive at barrier `ph` and wait until every CTA has; meanwhile run rounds
+// of the near-field queue if `near` (while it has items).  False when the
+// wait gave up (error flag 4) or a copy wait did.
+template <int D, int KER>
+__device__ __noinline__ bool persist_barrier(const PersistArgs& pa, int ph, bool near, bool& near_left, unsigned char* smem,
+                                PShared& sh) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(pa.sync + ph, 1u);
+  }
+  uint64_t t0 = threadIdx.x == 0 ? global_ns() : 0;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const bool all = ld_acquire_gpu(pa.sync + ph) >= gridDim.x;
+      sh.flag = all ? 1 : (global_ns() - t0 > kPersistWaitNs ? 2 : 0);
+    }
+    __syncthreads();
+    const int f = sh.flag;
+    __syncthreads();
+    if (f == 1) break;
+    if (f == 2) {
+      if (threadIdx.x == 0) atomicExch(pa.err, 4);
+      return false;
+    }
+    if (near && near_left) {
+      const int r = persist_drain<D, KER>(pa.near, pa.nnear, pa.near_total, pa.sync + kPersistSync - 2,
+                                          pa.gs_near, pa.near_group_bytes, smem, sh, pa.sync + ph);
+      if (r < 0) return false;
+      if (r == 0) near_left = false;
+      if (threadIdx.x == 0) t0 = global_ns();
+      continue;
+    }
+    if (threadIdx.x == 0) __nanosleep(256);
+  }
+  // the other CTAs' writes are now visible; order them before this CTA's
+  // bulk copies (async proxy) as well
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+  __syncthreads();
+  return true;
+}
+
+__device__ __forceinline__ void persist_up_items(const PersistArgs& pa, int h) {
+  for (int i = static_cast<int>(blockIdx.x); i < pa.up_cnt[h]; i += static_cast<int>(gridDim.x)) {
+    const int2 w = pa.work[pa.up_off[h] + i];
+    const ProbF32& p = pa.probs[w.x];
+    moments_body<float>(p.e, w.y, level_of(w.y) == p.J, p.L, p.count, p.pts, p.m_pad, p.xb, p.ynode, p.lo, p.iext,
+                        p.vinv, p.R, p.mom);
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ void persist_down_items(const PersistArgs& pa, int j) {
+  for (int i = static_cast<int>(blockIdx.x); i < pa.down_cnt[j]; i += static_cast<int>(gridDim.x)) {
+    const int2 w = pa.work[pa.down_off[j] + i];
+    const ProbF32& p = pa.probs[w.x];
+    downward_body<float>(p.e, w.y, level_of(w.y), p.jmin, p.J, p.L, p.count, p.pts, p.m_pad, p.ynode, p.lo, p.iext,
+                         p.loc, p.lco, p.vinv, p.R, p.yfar);
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ void persist_interleave(const PersistSeg* segs, int nseg, int64_t t0, int64_t stride) {
+  for (int s = 0; s < nseg; ++s) {
+    const PersistSeg& sg = segs[s];
+    const int ld = sg.a.ld;
+    const int64_t n = static_cast<int64_t>(sg.count) * ld * sg.rc;
+    const float* src = sg.ilv_src + static_cast<int64_t>(sg.a.first) * kRC * ld;
+    float* dst = const_cast<float*>(sg.a.q) + static_cast<int64_t>(sg.a.first) * sg.rc * ld;
+    for (int64_t t = t0; t < n; t += stride) sk::interleave_elem(src, ld, sg.rc, dst, t);
+  }
+}
+
+template <int D, int KER>
+__global__ void __launch_bounds__(kPersistThreads, 3) k_batch_persistent(const __grid_constant__ PersistArgs pa) {
+  extern __shared__ __align__(128) unsigned char psm[];
+  __shared__ PShared sh;
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < kPersistThreads / 32; ++k) {
+      sk::mbar_init(&sh.full[k][0], 1);
+      sk::mbar_init(&sh.full[k][1], 1);
+      sh.tiles[k] = 0;
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  const int64_t t0 = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  int ph = 0;
+  bool near_left = pa.near_total > 0;
+  // gather
+  const int64_t nel = static_cast<int64_t>(pa.Ltot) * kRC * pa.ld;
+  if (pa.io)
+    for (int64_t t = t0; t < nel; t += stride) gather_elem(pa.probs, pa.leaf_off, pa.P, pa.ld, pa.xb, t);
+  if (!persist_barrier<D, KER>(pa, ph++, false, near_left, psm, sh)) return;
+  // near-field charges; P2M of the leaves
+  persist_interleave(pa.near, pa.nnear, t0, stride);
+  if (pa.nup > 0) persist_up_items(pa, 0);
+  if (!persist_barrier<D, KER>(pa, ph++, false, near_left, psm, sh)) return;
+  // M2M by height
+  for (int h = 1; h < pa.nup; ++h) {
+    persist_up_items(pa, h);
+    if (!persist_barrier<D, KER>(pa, ph++, true, near_left, psm, sh)) return;
+  }
+  // M2L
+  if (pa.m2l_total > 0) {
+    persist_interleave(pa.m2l, pa.nm2l, t0, stride);
+    if (!persist_barrier<D, KER>(pa, ph++, true, near_left, psm, sh)) return;
+    if (persist_drain<D, KER>(pa.m2l, pa.nm2l, pa.m2l_total, pa.sync + kPersistSync - 1, pa.gs_m2l,
+                              pa.m2l_group_bytes, psm, sh, nullptr) < 0)
+      return;
+    if (!persist_barrier<D, KER>(pa, ph++, true, near_left, psm, sh)) return;
+  }
+  // L2L / L2P by level
+  for (int j = 0; j < pa.ndown; ++j) {
+    persist_down_items(pa, j);
+    if (!persist_barrier<D, KER>(pa, ph++, true, near_left, psm, sh)) return;
+  }
+  // the rest of the near field
+  if (near_left && persist_drain<D, KER>(pa.near, pa.nnear, pa.near_total, pa.sync + kPersistSync - 2, pa.gs_near,
+                                          pa.near_group_bytes, psm, sh, nullptr) < 0)
+    return;
+  if (!persist_barrier<D, KER>(pa, ph++, false, near_left, psm, sh)) return;
+  if (pa.io)
+    for (int64_t t = t0; t < nel; t += stride)
+      scatter_elem(pa.probs, pa.leaf_off, pa.P, pa.ld, pa.ynear, pa.yfar, t);
 }
 
 // x (caller order, column-major) -> xb[leaf][r][m_pad] for r in [r0, r0+Rc).
@@ -489,6 +732,77 @@ void launch_scatter_batched(const ProbF32* probs, const int* leaf_off, int P, in
                             const float* yfar, cudaStream_t s) {
   const int64_t total = static_cast<int64_t>(Ltot) * kRC * ld;
   k_scatter_batched<<<ceil_div(total, 256), 256, 0, s>>>(probs, leaf_off, P, Ltot, ld, ynear, yfar);
+}
+
+size_t persist_group_bytes(int D, int RC, int ld, int threads) { return sk::group_stage_bytes(D, RC, ld, threads); }
+
+namespace {
+
+template <int D>
+const void* persist_fn_d(int kernel) {
+  switch (kernel) {
+    case DWFMM_K_EXP: return reinterpret_cast<const void*>(k_batch_persistent<D, DWFMM_K_EXP>);
+    case DWFMM_K_MATERN32: return reinterpret_cast<const void*>(k_batch_persistent<D, DWFMM_K_MATERN32>);
+    default: return reinterpret_cast<const void*>(k_batch_persistent<D, DWFMM_K_GAUSS>);
+  }
+}
+
+const void* persist_fn(int D, int kernel) {
+  switch (D) {
+    case 4: return persist_fn_d<4>(kernel);
+    case 8: return persist_fn_d<8>(kernel);
+    case 10: return persist_fn_d<10>(kernel);
+    case 12: return persist_fn_d<12>(kernel);
+    case 16: return persist_fn_d<16>(kernel);
+    default: return persist_fn_d<20>(kernel);
+  }
+}
+
+template <int D>
+cudaError_t persist_launch_d(int kernel, const cudaLaunchConfig_t& cfg, const PersistArgs& pa) {
+  switch (kernel) {
+    case DWFMM_K_EXP: return cudaLaunchKernelEx(&cfg, k_batch_persistent<D, DWFMM_K_EXP>, pa);
+    case DWFMM_K_MATERN32: return cudaLaunchKernelEx(&cfg, k_batch_persistent<D, DWFMM_K_MATERN32>, pa);
+    default: return cudaLaunchKernelEx(&cfg, k_batch_persistent<D, DWFMM_K_GAUSS>, pa);
+  }
+}
+
+}  // namespace
+
+int persist_blocks_per_sm(int D, int kernel, size_t smem) {
+  const void* f = persist_fn(D, kernel);
+  if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, kPersistThreads, smem) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+cudaError_t launch_batch_persistent(int D, int kernel, const PersistArgs& pa, int grid, size_t smem,
+                                    cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(static_cast<unsigned>(grid));
+  cfg.blockDim = dim3(kPersistThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  switch (D) {
+    case 4: return persist_launch_d<4>(kernel, cfg, pa);
+    case 8: return persist_launch_d<8>(kernel, cfg, pa);
+    case 10: return persist_launch_d<10>(kernel, cfg, pa);
+    case 12: return persist_launch_d<12>(kernel, cfg, pa);
+    case 16: return persist_launch_d<16>(kernel, cfg, pa);
+    default: return persist_launch_d<20>(kernel, cfg, pa);
+  }
 }
 
 void launch_farfield(Plan& P, int Rc, bool fp64) {

@@ -38,7 +38,7 @@ EXPORTS = ("dwfmm_plan_create", "dwfmm_plan_set_nodes", "dwfmm_tree_build", "dwf
            "dwfmm_cg_begin", "dwfmm_cg_step", "dwfmm_cg_poll", "dwfmm_cg_result", "dwfmm_residual",
            "dwfmm_refine",
            "dwfmm_batch_create", "dwfmm_batch_matvec", "dwfmm_batch_info", "dwfmm_batch_shape",
-           "dwfmm_batch_cg_step",
+           "dwfmm_batch_cg_step", "dwfmm_batch_engine", "dwfmm_batch_set_engine",
            "dwfmm_batch_destroy",
            "dwfmm_evaluate")
 
@@ -96,6 +96,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "dwfmm_batch_info": (i32, [P, C.POINTER(i32), P, C.POINTER(i64)]),
         "dwfmm_batch_cg_step": (i32, [P, i32, P]),
         "dwfmm_batch_shape": (i32, [P, P]),
+        "dwfmm_batch_engine": (i32, [P, P, P, P]),
+        "dwfmm_batch_set_engine": (i32, [P, i32]),
         "dwfmm_batch_destroy": (i32, [P]),
         "dwfmm_evaluate": (i32, [P, P, i64, i64, P, i64, P, i64, i32, P]),
     }
@@ -468,6 +470,30 @@ class Batch:
         return {"split": bool(split.value), "tune_ms": [tune[0], tune[1]], "leaves": int(leaves.value),
                 "near_shape": {"per_class": bool(shape[0]), "threads": int(shape[1])},
                 "m2l_shape": {"per_class": bool(shape[2]), "threads": int(shape[3])}}
+
+    def engine(self):
+        """The matvec engine in use ("graph" or "persistent"), whether the
+        persistent one is available, the creation timings (ms) of both and the
+        persistent launch's CTAs and group widths."""
+        eng = (C.c_int32 * 2)()
+        ms = (C.c_double * 2)()
+        launch = (C.c_int32 * 3)()
+        st = self._l.dwfmm_batch_engine(self.h, eng, ms, launch)
+        if st != OK:
+            raise DwfmmError(st, self._l.dwfmm_status_string(st).decode())
+        return {"engine": "persistent" if eng[0] else "graph", "persistent_available": bool(eng[1]),
+                "ms": {"graph": ms[0], "persistent": ms[1]},
+                "persistent_launch": {"ctas": int(launch[0]), "near_threads": int(launch[1]),
+                                      "m2l_threads": int(launch[2])}}
+
+    def set_engine(self, engine: str):
+        """Use "graph" (captured launches) or "persistent" (one cooperative launch)."""
+        if engine not in ("graph", "persistent"):
+            raise ValueError("engine must be 'graph' or 'persistent'")
+        st = self._l.dwfmm_batch_set_engine(self.h, 1 if engine == "persistent" else 0)
+        if st != OK:
+            msg = self._l.dwfmm_last_error(self.plans[0].h).decode() if self.plans else ""
+            raise DwfmmError(st, msg or self._l.dwfmm_status_string(st).decode())
 
     def close(self):
         if getattr(self, "h", None):

@@ -80,3 +80,58 @@ def test_batch_matches_oracle_on_small_problems():
         pb = o.make_problem(X, w.kernel, o.weights_inv_gamma(w.gamma), w.q, w.leaf, w.eta)
         assert o.rel_err(ys[i].cpu().numpy(), o.fmm_matvec(pb, f)) <= FP32_TOL
     b.close()
+
+
+def test_persistent_engine_equals_launch_graph():
+    """The whole batch matvec as one persistent cooperative launch (phases
+    separated by grid-wide barriers, near-field groups taken from a work queue
+    while the far-field phases wait) sums every target in the order of the
+    captured launches: both engines give the same result bit for bit, on
+    repeated calls, and in batched CG iterations."""
+    import torch
+    from paper_2402_09531_gb300 import Batch
+    probs, plans, xs, ys, data = _setup(24, 12000)
+    b = Batch(plans, [w.nrhs for w in probs])
+    e = b.engine()
+    assert e["persistent_available"], e
+    assert e["ms"]["graph"] > 0 and e["ms"]["persistent"] > 0, e
+    launch = e["persistent_launch"]
+    assert launch["ctas"] > 0 and launch["near_threads"] in (32, 64, 128) and launch["m2l_threads"] in (32, 64, 128)
+    results = {}
+    for eng in ("graph", "persistent", "graph", "persistent"):
+        b.set_engine(eng)
+        assert b.engine()["engine"] == eng
+        out = [torch.full_like(x, float("nan")) for x in xs]
+        b.matvec(xs, out)
+        torch.cuda.synchronize()
+        if eng in results:
+            for y1, y2 in zip(results[eng], out):
+                assert torch.equal(y1, y2)
+        results[eng] = out
+    for i, (yg, yp) in enumerate(zip(results["graph"], results["persistent"])):
+        assert torch.isfinite(yp).all(), i
+        assert torch.equal(yg, yp), (i, float((yg - yp).abs().max()))
+    # the oracle on the smallest problem
+    k = min(range(len(probs)), key=lambda i: probs[i].n)
+    w, X, f = data[k]
+    pb = o.make_problem(X, w.kernel, o.weights_inv_gamma(w.gamma), w.q, w.leaf, w.eta)
+    assert o.rel_err(results["persistent"][k].cpu().numpy(), o.fmm_matvec(pb, f)) <= FP32_TOL
+    # batched CG: same iterates with either engine
+    lam = 1e-1
+    sols = {}
+    for eng in ("graph", "persistent"):
+        b.set_engine(eng)
+        for p, x in zip(plans, xs):
+            p.cg_begin(lam, x, rtol=1e-6)
+        b.cg_step(12)
+        torch.cuda.synchronize()
+        cs = []
+        for p, x in zip(plans, xs):
+            c = torch.empty_like(x)
+            p.cg_result(c)
+            cs.append(c)
+        torch.cuda.synchronize()
+        sols[eng] = cs
+    for c1, c2 in zip(sols["graph"], sols["persistent"]):
+        assert torch.equal(c1, c2)
+    b.close()
