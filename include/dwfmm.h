@@ -295,17 +295,24 @@ dwfmm_status dwfmm_batch_shape(dwfmm_batch batch, int32_t* shape);
  * from a second work queue while they wait, and all right-hand-side classes
  * share the queues; near-field and coupling target groups run on groups of
  * 32, 64 or 128 threads of a CTA.  Both engines sum every target in the same
- * order: their results are equal bit for bit.  At creation the persistent
- * engine is timed at every near-field group width against the graph, and the
- * faster engine is used (if the device can launch it and a stream capture
- * holds it).
+ * order: their results are equal bit for bit.  When the batch's fused near
+ * field and couplings take at least 2 ms (the launch tuner's time), creation
+ * times the persistent engine at every near-field group width against the
+ * graph (both without the gather and scatter) and uses the faster, if the
+ * device can launch it and a stream capture holds it; smaller batches (a
+ * serving loop rebuilds them often) start on the graph and tune the
+ * persistent engine at the first request for it.
  * dwfmm_batch_engine: engine[0] the engine in use, engine[1] 1 if the
- *   persistent engine is available; ms[0], ms[1] the best timed matvec of
- *   each engine at creation (-1 if not timed); launch[0..2] the persistent
- *   launch's CTAs and the near-field and coupling group widths (0 if not
- *   available).  Host arrays of 2, 2 and 3 elements.
+ *   persistent engine is available (0 also while it is not tuned); ms[0],
+ *   ms[1] the best timed matvec of each engine (-1 if not timed);
+ *   launch[0..2] the persistent launch's CTAs and the near-field and
+ *   coupling group widths (0 if not available).  Host arrays of 2, 2 and 3
+ *   elements.
  * dwfmm_batch_set_engine: selects engine 0 or 1 for later matvecs and
- *   batched CG steps; DWFMM_ERR_STATE if 1 is not available.
+ *   batched CG steps; the first selection of 1 on a batch whose persistent
+ *   engine is not tuned yet tunes it then (synchronising the device first:
+ *   the timing runs use the batch's buffers); DWFMM_ERR_STATE if 1 is not
+ *   available.
  * Errors: INVALID_ARG (NULL batch or output, engine outside 0..1).  No
  * counterpart in the paper (a scheduling choice). */
 dwfmm_status dwfmm_batch_engine(dwfmm_batch batch, int32_t* engine, double* ms, int32_t* launch);

@@ -63,6 +63,7 @@ struct Batch {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   // persistent engine: the whole matvec as one cooperative launch
+  bool persist_tried = false;    // the persistent engine was tuned
   bool persist_ok = false;       // eligible (launch and capture worked, no wait gave up)
   bool persistent = false;       // the engine in use
   PersistArgs pa{};
@@ -279,6 +280,10 @@ void tune_shapes(Batch& B) {
 
 // --- persistent engine -------------------------------------------------------
 
+// Fused near-field + coupling time (ms, from the launch tuner) from which the
+// persistent engine is tuned at creation.
+constexpr double kPersistTuneMinMs = 2.0;
+
 int pow2_width(int t) { return t <= 32 ? 32 : t <= 64 ? 64 : 128; }
 
 // Arguments of the persistent kernel with near-field groups of gs_near threads
@@ -424,6 +429,7 @@ bool take_device_error(Batch& B) {
 // Both are timed without the gather and the scatter (no caller buffers
 // exist yet; those two phases are the same elementwise work in both).
 void tune_persistent(Batch& B) {
+  B.persist_tried = true;
   B.persist_ok = false;
   B.persistent = false;
   int dev = 0, coop = 0;
@@ -640,8 +646,10 @@ void batch_create(Batch& B, Plan* const* plans, const int32_t* nrhs, int count) 
   enqueue_matvec(B);
   DW_CUDA(cudaStreamEndCapture(B.stream, &B.graph));
   DW_CUDA(cudaGraphInstantiate(&B.exec, B.graph, 0));
-  // then the persistent engine against it
-  tune_persistent(B);
+  // then the persistent engine against it, for batches whose fused work
+  // takes long enough to repay the tuning (a serving loop rebuilds small
+  // batches often; there the engine is tuned only when asked for)
+  if (std::min(B.tune_ms[0], B.tune_ms[1]) >= kPersistTuneMinMs) tune_persistent(B);
 }
 
 void batch_matvec(Batch& B, const double* const* x, double* const* y, cudaStream_t s) {
@@ -662,6 +670,12 @@ void batch_matvec(Batch& B, const double* const* x, double* const* y, cudaStream
 }
 
 void batch_set_engine(Batch& B, int persistent) {
+  if (persistent && !B.persist_tried) {
+    // the tuning runs overwrite the batch's buffers: nothing may be in flight
+    DW_CUDA(cudaDeviceSynchronize());
+    tune_persistent(B);
+    B.persistent = false;
+  }
   if (persistent && !B.persist_ok) fail(DWFMM_ERR_STATE, "the persistent engine is not available for this batch");
   if (B.persistent == (persistent != 0)) return;
   B.persistent = persistent != 0;

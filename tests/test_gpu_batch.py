@@ -92,8 +92,9 @@ def test_persistent_engine_equals_launch_graph():
     from paper_2402_09531_gb300 import Batch
     probs, plans, xs, ys, data = _setup(24, 12000)
     b = Batch(plans, [w.nrhs for w in probs])
+    b.set_engine("persistent")      # tunes the persistent engine if creation did not
     e = b.engine()
-    assert e["persistent_available"], e
+    assert e["persistent_available"] and e["engine"] == "persistent", e
     assert e["ms"]["graph"] > 0 and e["ms"]["persistent"] > 0, e
     launch = e["persistent_launch"]
     assert launch["ctas"] > 0 and launch["near_threads"] in (32, 64, 128) and launch["m2l_threads"] in (32, 64, 128)
