@@ -933,7 +933,15 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    res = oracle_sample(args.workload, args.steps, args.warmup)
+    # in a child process with one BLAS thread per core's worker: forking the
+    # per-core workers from a process whose BLAS thread pool is running can
+    # hang them, and each worker's own threads would oversubscribe the cores
+    p = start_oracle_subprocess(args.workload, args.steps, args.warmup)
+    res = finish_oracle_subprocess(p, timeout=300.0 + 120.0 * (args.steps + args.warmup))
+    if res is None:
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle sample did not finish in time"}),
+              flush=True)
+        return
     w = workload(args.workload)
     value = res["units_per_step"] / res["s_per_step"]
     line = {

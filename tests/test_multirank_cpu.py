@@ -81,3 +81,18 @@ def test_traffic_is_reported_only_for_the_captured_kernel_source():
     for b, src, sha, wl, fn in bench._traffic_records():
         assert b > 0 and src.endswith(".cu") and len(sha) == 16
     assert bench.recorded_traffic("p2p_tc.cu", "no-such-workload") is None
+
+
+def test_reference_arm_prints_its_line_on_rank_zero():
+    """Rank 0 runs the oracle sample in a child process with one BLAS thread
+    (forking the per-core workers from a process with a running BLAS thread
+    pool could hang them) and prints one JSON line."""
+    import json
+    env = dict(os.environ, RANK="0", WORLD_SIZE="1", LOCAL_RANK="0")
+    p = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload", "small",
+                        "--steps", "1", "--warmup", "0"], env=env, capture_output=True, text=True, timeout=300)
+    assert p.returncode == 0, p.stderr[-2000:]
+    line = json.loads(p.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0
