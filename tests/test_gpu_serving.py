@@ -308,3 +308,28 @@ def test_poll_after_a_new_begin_waits_for_its_first_step():
     ready, st, it, rr = p.cg_poll()
     assert ready and int(it[0]) <= 4
     p.close()
+
+
+def test_persistent_batch_engine_on_serving_shapes():
+    """The persistent batch engine on the serving stream's shape (d = 16,
+    exponential kernel, one right-hand side, small problems): bit for bit the
+    graph engine's matvec."""
+    import torch
+    from paper_2402_09531_gb300 import Batch
+    reqs = _requests([1400, 2100, 1000, 2600, 1700], seed0=120)
+    plans, fs = _mixed_plans(reqs)
+    b = Batch(plans, [1] * len(plans))
+    out = {}
+    for eng in ("graph", "persistent"):
+        b.set_engine(eng)
+        ys = [torch.full_like(f, float("nan")) for f in fs]
+        b.matvec(fs, ys)
+        torch.cuda.synchronize()
+        out[eng] = ys
+    assert b.engine()["persistent_available"]
+    for yg, yp in zip(out["graph"], out["persistent"]):
+        assert torch.isfinite(yp).all()
+        assert torch.equal(yg, yp)
+    b.close()
+    for p in plans:
+        p.close()
