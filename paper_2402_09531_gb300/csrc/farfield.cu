@@ -430,9 +430,10 @@ __device__ __noinline__ int persist_drain(const PersistSeg* segs, int nseg, int 
   return bad ? -1 : (emp ? 0 : 1);
 }
 
-// Arrive at barrier `ph` and wait until every CTA has; meanwhile run rounds
-// of the near-field queue if `near` (while it has items).  False when the
-// wait gave up (error flag 4) or a copy wait did.
+// Arrive at barrier `ph` and wait until every CTA has; meanwhile, if `near`,
+// the CTA's groups take near-field items from their queue until the barrier
+// completes or the queue is empty.  False when the wait gave up (error flag
+// 4) or a copy wait did.
 template <int D, int KER>
 __device__ __noinline__ bool persist_barrier(const PersistArgs& pa, int ph, bool near, bool& near_left, unsigned char* smem,
                                 PShared& sh) {
