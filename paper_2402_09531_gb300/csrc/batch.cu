@@ -394,25 +394,23 @@ void drop_graph(cudaGraph_t* g, cudaGraphExec_t* e) {
   *g = nullptr;
 }
 
-// Best of two timed replays of a captured matvec (after one untimed).
+// Best of two timed replays of a captured matvec (after one untimed); -1 if
+// a launch or the timing failed (the events are released either way).
 double time_exec(Batch& B, cudaGraphExec_t e) {
-  cudaEvent_t a, b;
-  DW_CUDA(cudaEventCreate(&a));
-  DW_CUDA(cudaEventCreate(&b));
-  DW_CUDA(cudaGraphLaunch(e, B.stream));
+  cudaEvent_t a = nullptr, b = nullptr;
   float best = 1e30f;
-  for (int rep = 0; rep < 2; ++rep) {
-    DW_CUDA(cudaEventRecord(a, B.stream));
-    DW_CUDA(cudaGraphLaunch(e, B.stream));
-    DW_CUDA(cudaEventRecord(b, B.stream));
-    DW_CUDA(cudaEventSynchronize(b));
+  bool ok = cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess &&
+            cudaGraphLaunch(e, B.stream) == cudaSuccess;
+  for (int rep = 0; ok && rep < 2; ++rep) {
     float ms = 0.f;
-    DW_CUDA(cudaEventElapsedTime(&ms, a, b));
-    best = std::min(best, ms);
+    ok = cudaEventRecord(a, B.stream) == cudaSuccess && cudaGraphLaunch(e, B.stream) == cudaSuccess &&
+         cudaEventRecord(b, B.stream) == cudaSuccess && cudaEventSynchronize(b) == cudaSuccess &&
+         cudaEventElapsedTime(&ms, a, b) == cudaSuccess;
+    if (ok) best = std::min(best, ms);
   }
-  cudaEventDestroy(a);
-  cudaEventDestroy(b);
-  return best;
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  return ok ? best : -1.0;
 }
 
 // Reads and clears the batch's error flag (a bounded device wait gave up).
@@ -440,6 +438,7 @@ void tune_persistent(Batch& B) {
   if (!capture_engine(B, false, false, &g, &e)) fail(DWFMM_ERR_CUDA, "capture of the batch matvec failed");
   B.engine_ms[0] = time_exec(B, e);
   drop_graph(&g, &e);
+  if (B.engine_ms[0] < 0.0) fail(DWFMM_ERR_CUDA, "the batch matvec failed while it was timed");
   if (!coop) return;
   B.psync.alloc(kPersistSync);
   const int gs_m2l = pow2_width(B.thr_m2l);
@@ -451,6 +450,12 @@ void tune_persistent(Batch& B) {
     if (!capture_engine(B, true, false, &g, &e)) return;
     const double ms = time_exec(B, e);
     drop_graph(&g, &e);
+    // a launch the device refuses leaves the engine unavailable (a fault is
+    // sticky and ends the creation at the next checked call)
+    if (ms < 0.0) {
+      (void)cudaGetLastError();
+      return;
+    }
     if (take_device_error(B)) return;
     if (ms < best) {
       best = ms;
